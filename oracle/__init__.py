@@ -1,0 +1,248 @@
+"""FP64 oracle of the FoE Poisson denoiser: ctypes wrapper around ``foe_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline legs may import this package.  The CUDA library never loads it
+and it never loads the CUDA library.
+
+The C file is compiled here with gcc (``-O3 -ffp-contract=off``, no fast-math, so the FP64
+results are the same on x86-64 and aarch64 hosts).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "foe_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+MODEL_DIRECT, MODEL_ANS_L2, MODEL_ANS_IDIV, MODEL_AUTO = 0, 1, 2, 3
+BC_SYMMETRIC, BC_ZERO = 0, 1
+
+_dp = C.POINTER(C.c_double)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nf", C.c_int), ("k", _dp), ("alpha", _dp),
+        ("H", C.c_int), ("W", C.c_int), ("bc", C.c_int), ("model", C.c_int),
+        ("lam", C.c_double), ("tau", C.c_double), ("gamma", C.c_double),
+        ("nthreads", C.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liborc.so`` (idempotent)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+                    "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm", "-lpthread"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> C.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            for name in ("orc_anscombe1", "orc_ic1", "orc_ic_deriv1", "orc_rho", "orc_rho1", "orc_rho2"):
+                getattr(L, name).restype = C.c_double
+                getattr(L, name).argtypes = [C.c_double]
+            L.orc_pad_index.restype = C.c_long
+            L.orc_pad_index.argtypes = [C.c_long, C.c_long, C.c_int]
+            L.orc_anscombe.argtypes = [C.c_long, _dp, _dp]
+            L.orc_inverse.argtypes = [C.c_long, _dp, _dp]
+            L.orc_responses.argtypes = [C.c_int, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, C.c_int]
+            L.orc_adjoint.argtypes = [C.c_int, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, C.c_int]
+            L.orc_prior_energy.restype = C.c_double
+            L.orc_prior_energy.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int, _dp, C.c_int, C.c_int]
+            L.orc_prior_grad.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, C.c_int]
+            L.orc_data_energy.restype = C.c_double
+            L.orc_data_energy.argtypes = [C.c_int, C.c_double, C.c_long, _dp, _dp]
+            L.orc_data_grad.argtypes = [C.c_int, C.c_double, C.c_long, _dp, _dp, _dp]
+            L.orc_prox.argtypes = [C.c_int, C.c_double, C.c_long, _dp, _dp, _dp]
+            L.orc_energy.restype = C.c_double
+            L.orc_energy.argtypes = [C.POINTER(Params), _dp, _dp]
+            L.orc_energy_grad.restype = C.c_double
+            L.orc_energy_grad.argtypes = [C.POINTER(Params), _dp, _dp, _dp]
+            L.orc_ipiano_step.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp]
+            L.orc_ipiano.restype = C.c_int
+            L.orc_ipiano.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_int, _dp]
+            L.orc_denoise.restype = C.c_int
+            L.orc_denoise.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, _dp]
+            L.orc_lipschitz.restype = C.c_double
+            L.orc_lipschitz.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int]
+            L.orc_psnr.restype = C.c_double
+            L.orc_psnr.argtypes = [C.c_long, _dp, _dp, C.c_double]
+            _lib = L
+    return _lib
+
+
+def _d(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+# ---- scalar maps (Eq. Anscombetransform, Eq. invAns, I_C', Eq. STfunc) ----
+def anscombe(y):
+    y = _d(y)
+    v = np.empty_like(y)
+    lib().orc_anscombe(y.size, _p(y), _p(v))
+    return v
+
+
+def inverse(z):
+    z = _d(z)
+    x = np.empty_like(z)
+    lib().orc_inverse(z.size, _p(z), _p(x))
+    return x
+
+
+def ic(z: float) -> float:
+    return lib().orc_ic1(float(z))
+
+
+def ic_deriv(z: float) -> float:
+    return lib().orc_ic_deriv1(float(z))
+
+
+def rho(z: float) -> float:
+    return lib().orc_rho(float(z))
+
+
+def rho1(z: float) -> float:
+    return lib().orc_rho1(float(z))
+
+
+def rho2(z: float) -> float:
+    return lib().orc_rho2(float(z))
+
+
+def pad_index(i: int, n: int, bc: int) -> int:
+    return lib().orc_pad_index(i, n, bc)
+
+
+# ---- linear operators (Eq. FOEmodel, Sec. 2.5.2) ----
+def _filters(k) -> np.ndarray:
+    k = _d(k)
+    return k.reshape(k.shape[0], 49)
+
+
+def responses(k, u, bc=BC_SYMMETRIC, nthreads=None):
+    k = _filters(k)
+    u = _d(u)
+    H, W = u.shape
+    r = np.empty((k.shape[0], H, W))
+    lib().orc_responses(k.shape[0], _p(k), H, W, _p(u), bc, _p(r), nthreads or default_threads())
+    return r
+
+
+def adjoint(k, psi, bc=BC_SYMMETRIC, nthreads=None):
+    k = _filters(k)
+    psi = _d(psi)
+    nf, H, W = psi.shape
+    g = np.empty((H, W))
+    lib().orc_adjoint(nf, _p(k), H, W, _p(psi), bc, _p(g), nthreads or default_threads())
+    return g
+
+
+def prior_energy(k, alpha, u, bc=BC_SYMMETRIC, nthreads=None) -> float:
+    k, a, u = _filters(k), _d(alpha), _d(u)
+    H, W = u.shape
+    return lib().orc_prior_energy(k.shape[0], _p(k), _p(a), H, W, _p(u), bc, nthreads or default_threads())
+
+
+def prior_grad(k, alpha, u, bc=BC_SYMMETRIC, nthreads=None):
+    k, a, u = _filters(k), _d(alpha), _d(u)
+    H, W = u.shape
+    g = np.empty((H, W))
+    lib().orc_prior_grad(k.shape[0], _p(k), _p(a), H, W, _p(u), bc, _p(g), nthreads or default_threads())
+    return g
+
+
+def data_energy(model, lam, u, d) -> float:
+    u, d = _d(u), _d(d)
+    return lib().orc_data_energy(model, float(lam), u.size, _p(u), _p(d))
+
+
+def data_grad(model, lam, u, d):
+    u, d = _d(u), _d(d)
+    g = np.empty_like(u)
+    lib().orc_data_grad(model, float(lam), u.size, _p(u), _p(d), _p(g))
+    return g
+
+
+def prox(model, tl, ut, d):
+    ut, d = _d(ut), _d(d)
+    out = np.empty_like(ut)
+    lib().orc_prox(model, float(tl), ut.size, _p(ut), _p(d), _p(out))
+    return out
+
+
+# ---- solver ----
+class Problem:
+    """Holds the parameter block and keeps its arrays alive."""
+
+    def __init__(self, k, alpha, H, W, *, bc=BC_SYMMETRIC, model=MODEL_ANS_L2, lam=1.0, tau=1e-3,
+                 gamma=0.8, nthreads=None):
+        self.k = _filters(k)
+        self.alpha = _d(alpha)
+        self.p = Params(self.k.shape[0], _p(self.k), _p(self.alpha), int(H), int(W), int(bc), int(model),
+                        float(lam), float(tau), float(gamma), int(nthreads or default_threads()))
+
+    def energy(self, u, d) -> float:
+        u, d = _d(u), _d(d)
+        return lib().orc_energy(C.byref(self.p), _p(u), _p(d))
+
+    def energy_grad(self, u, d):
+        u, d = _d(u), _d(d)
+        g = np.empty_like(u)
+        e = lib().orc_energy_grad(C.byref(self.p), _p(u), _p(d), _p(g))
+        return e, g
+
+    def step(self, d, u, u_prev):
+        d, u, up = _d(d), _d(u), _d(u_prev)
+        un = np.empty_like(u)
+        lib().orc_ipiano_step(C.byref(self.p), _p(d), _p(u), _p(up), _p(un))
+        return un
+
+    def ipiano(self, d, u0, u_prev0, iters, trace=False):
+        d = _d(d)
+        u = _d(u0).copy()
+        up = _d(u_prev0).copy()
+        e = np.empty(iters + 1) if trace else None
+        lib().orc_ipiano(C.byref(self.p), _p(d), _p(u), _p(up), int(iters), _p(e) if trace else None)
+        return (u, up, e) if trace else (u, up)
+
+    def denoise(self, y, peak, iters, zero_c=0.0):
+        y = _d(y)
+        x = np.empty_like(y)
+        used = lib().orc_denoise(C.byref(self.p), _p(y), float(peak), float(zero_c), int(iters), _p(x))
+        return x, used
+
+
+def lipschitz(k, alpha, bc=BC_SYMMETRIC, ngrid=512) -> float:
+    k, a = _filters(k), _d(alpha)
+    return lib().orc_lipschitz(k.shape[0], _p(k), _p(a), bc, ngrid)
+
+
+def psnr(a, b, peak) -> float:
+    a, b = _d(a), _d(b)
+    return lib().orc_psnr(a.size, _p(a), _p(b), float(peak))

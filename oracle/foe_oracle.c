@@ -1,0 +1,435 @@
+/*
+ * FP64 oracle of the FoE-regularised Poisson denoiser (Feng, Qiao, Chen, arXiv:1609.05722).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the CUDA path is
+ * checked against.  Only the test suite, the smoke check and the benchmark's CPU-baseline
+ * legs may load it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Every quantity is computed in double precision by direct loops, in the order the paper
+ * states it.  No blocking, no fusion, no reordering beyond the formulas.  The only
+ * parallelism is an optional split of image rows over threads; every output element is
+ * computed by the same sequence of operations whatever the thread count, so results do not
+ * depend on it.
+ *
+ * Conventions (readings of places where the paper is silent; each is listed in the design
+ * notes):
+ *   - images are row-major H x W;
+ *   - filters are convolution kernels, k[i*49 + (a+3)*7 + (b+3)] = k_i(a, b), a, b in -3..3,
+ *     and (k * u)_p = sum_{a,b} k(a, b) u(p - (a, b))  (Sec. 2.3, Eq. FOEmodel: "convolution");
+ *   - responses exist only at the N pixels of the image (K_i is N x N, Sec. 2.5.2); they are
+ *     taken on a padded image P u.  bc = 0: half-sample symmetric padding (index -1 -> 0,
+ *     -2 -> 1, ...); bc = 1: zero padding.  K_i = K_i,valid P and K_i^T = P^T K_i,valid^T;
+ *   - model 0 = direct I-divergence model (Eq. straightforward), 1 = Anscombe-domain
+ *     quadratic model (Eq. overallModel), 2 = Anscombe-domain I-divergence model (Eq. lowcase,
+ *     with the weights alpha_i kept as in Eq. FOEscheme).
+ *
+ * Parity pins: see the "-m 'not gpu'" oracle tests.  Every function below is pinned.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KS 7
+#define ORC_KK 49
+#define ORC_R 3
+
+/* ------------------------------------------------------------------------------------------
+ * Scalars: Anscombe transform (Eq. Anscombetransform), closed-form unbiased inverse (Eq.
+ * invAns) and its derivative (Sec. 3.2, I_C'), potential rho and its derivatives (Eq. STfunc,
+ * Sec. 2.5.2).
+ * ---------------------------------------------------------------------------------------- */
+double orc_anscombe1(double y) { return 2.0 * sqrt(y + 3.0 / 8.0); }
+
+double orc_ic1(double z)
+{
+    const double s = sqrt(1.5);
+    return 0.25 * z * z + 0.25 * s / z - (11.0 / 8.0) / (z * z) + (5.0 / 8.0) * s / (z * z * z) - 0.125;
+}
+
+double orc_ic_deriv1(double z)
+{
+    const double s = sqrt(1.5);
+    return 0.5 * z - 0.25 * s / (z * z) + (11.0 / 4.0) / (z * z * z) - (15.0 / 8.0) * s / (z * z * z * z);
+}
+
+double orc_rho(double z) { return log1p(z * z); }
+double orc_rho1(double z) { return 2.0 * z / (1.0 + z * z); }
+double orc_rho2(double z)
+{
+    const double q = 1.0 + z * z;
+    return 2.0 * (1.0 - z * z) / (q * q);
+}
+
+void orc_anscombe(long n, const double *y, double *v)
+{
+    for (long i = 0; i < n; ++i) v[i] = orc_anscombe1(y[i]);
+}
+
+/* x = I_C(max(z, sqrt(3/2))): the clamp keeps the output >= 0 (I_C(sqrt(3/2)) = 0). */
+void orc_inverse(long n, const double *z, double *x)
+{
+    const double zmin = sqrt(1.5);
+    for (long i = 0; i < n; ++i) x[i] = orc_ic1(z[i] > zmin ? z[i] : zmin);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Padding operator P.
+ * ---------------------------------------------------------------------------------------- */
+long orc_pad_index(long i, long n, int bc)
+{
+    if (bc == 1) return (i >= 0 && i < n) ? i : -1;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -1 - i;
+        if (i >= n) i = 2 * n - 1 - i;
+    }
+    return i;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Row-parallel helper.
+ * ---------------------------------------------------------------------------------------- */
+typedef void (*orc_rowfn)(void *ctx, long r0, long r1);
+typedef struct { orc_rowfn fn; void *ctx; long r0, r1; } orc_job;
+
+static void *orc_job_run(void *p)
+{
+    orc_job *j = (orc_job *)p;
+    j->fn(j->ctx, j->r0, j->r1);
+    return NULL;
+}
+
+static void orc_par_rows(long nrows, int nthreads, orc_rowfn fn, void *ctx)
+{
+    if (nthreads <= 1 || nrows < 2 * nthreads) {
+        fn(ctx, 0, nrows);
+        return;
+    }
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    orc_job jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].r0 = nrows * t / nthreads;
+        jobs[t].r1 = nrows * (t + 1) / nthreads;
+    }
+    int started[256];
+    for (int t = 0; t < nthreads; ++t) started[t] = pthread_create(&th[t], NULL, orc_job_run, &jobs[t]) == 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (started[t]) pthread_join(th[t], NULL);
+        else orc_job_run(&jobs[t]);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * K_i u: r(y, x) = sum_{a,b} k_i(a, b) (P u)(y - a, x - b) for (y, x) in the image.
+ * Each output accumulates its 49 products in tap order (a, then b); the loop over x is innermost
+ * only so that the compiler can vectorise it; this does not change any element's arithmetic.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int nf;
+    const double *k;  /* nf x 49 */
+    const double *pu; /* padded image, (H+6) x (W+6), origin at (-3, -3) */
+    int H, W;
+    double *r;        /* nf x H x W */
+} orc_resp_ctx;
+
+static void orc_resp_rows(void *c, long r0, long r1)
+{
+    orc_resp_ctx *q = (orc_resp_ctx *)c;
+    const long PW = q->W + 2 * ORC_R;
+    for (int i = 0; i < q->nf; ++i)
+        for (long y = r0; y < r1; ++y) {
+            double *row = q->r + (size_t)i * q->H * q->W + y * q->W;
+            for (long x = 0; x < q->W; ++x) row[x] = 0.0;
+            for (int a = -ORC_R; a <= ORC_R; ++a)
+                for (int b = -ORC_R; b <= ORC_R; ++b) {
+                    const double kv = q->k[(size_t)i * ORC_KK + (a + ORC_R) * ORC_KS + (b + ORC_R)];
+                    const double *src = q->pu + (y - a + ORC_R) * PW + (ORC_R - b);
+                    for (long x = 0; x < q->W; ++x) row[x] += kv * src[x];
+                }
+        }
+}
+
+static void orc_pad_image(int H, int W, const double *u, int bc, double *pu)
+{
+    const long PW = W + 2 * ORC_R;
+    for (long yp = -ORC_R; yp < H + ORC_R; ++yp)
+        for (long xp = -ORC_R; xp < W + ORC_R; ++xp) {
+            long sy = orc_pad_index(yp, H, bc), sx = orc_pad_index(xp, W, bc);
+            pu[(yp + ORC_R) * PW + (xp + ORC_R)] = (sy < 0 || sx < 0) ? 0.0 : u[sy * W + sx];
+        }
+}
+
+/* r[i*H*W + p] = (K_i u)_p for all filters. */
+void orc_responses(int nf, const double *k, int H, int W, const double *u, int bc, double *r, int nthreads)
+{
+    double *pu = (double *)malloc(sizeof(double) * (size_t)(H + 2 * ORC_R) * (W + 2 * ORC_R));
+    if (!pu) return;
+    orc_pad_image(H, W, u, bc, pu);
+    orc_resp_ctx c = {nf, k, pu, H, W, r};
+    orc_par_rows(H, nthreads, orc_resp_rows, &c);
+    free(pu);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * K^T psi = sum_i P^T K_i,valid^T psi_i.
+ *   h(q') = sum_i sum_{a,b} k_i(a, b) psi_i(q' + (a, b)) over q' + (a, b) in the image, for
+ *           every padded position q' (3-pixel border);
+ *   g(q)  = sum of h(q') over the padded positions q' that P maps to q.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int nf;
+    const double *k;
+    const double *psi;
+    int H, W;
+    double *h; /* (H+6) x (W+6), origin at (-3, -3) */
+} orc_adj_ctx;
+
+static void orc_adj_rows(void *c, long r0, long r1)
+{
+    orc_adj_ctx *q = (orc_adj_ctx *)c;
+    const long PW = q->W + 2 * ORC_R;
+    for (long row = r0; row < r1; ++row) {
+        const long yp = row - ORC_R;
+        double *hrow = q->h + row * PW; /* hrow[xp + 3] = h(yp, xp) */
+        for (long j = 0; j < PW; ++j) hrow[j] = 0.0;
+        for (int i = 0; i < q->nf; ++i)
+            for (int a = -ORC_R; a <= ORC_R; ++a) {
+                const long py = yp + a;
+                if (py < 0 || py >= q->H) continue;
+                const double *prow = q->psi + (size_t)i * q->H * q->W + py * q->W;
+                for (int b = -ORC_R; b <= ORC_R; ++b) {
+                    const double kv = q->k[(size_t)i * ORC_KK + (a + ORC_R) * ORC_KS + (b + ORC_R)];
+                    /* xp + b must lie in [0, W) */
+                    long x0 = -ORC_R, x1 = q->W + ORC_R;
+                    if (x0 < -b) x0 = -b;
+                    if (x1 > q->W - b) x1 = q->W - b;
+                    for (long xp = x0; xp < x1; ++xp) hrow[xp + ORC_R] += kv * prow[xp + b];
+                }
+            }
+    }
+}
+
+void orc_adjoint(int nf, const double *k, int H, int W, const double *psi, int bc, double *g, int nthreads)
+{
+    const long PH = H + 2 * ORC_R, PW = W + 2 * ORC_R;
+    double *h = (double *)malloc(sizeof(double) * (size_t)PH * PW);
+    if (!h) return;
+    orc_adj_ctx c = {nf, k, psi, H, W, h};
+    orc_par_rows(PH, nthreads, orc_adj_rows, &c);
+    for (long i = 0; i < (long)H * W; ++i) g[i] = 0.0;
+    for (long yp = -ORC_R; yp < H + ORC_R; ++yp)
+        for (long xp = -ORC_R; xp < W + ORC_R; ++xp) {
+            long sy = orc_pad_index(yp, H, bc), sx = orc_pad_index(xp, W, bc);
+            if (sy < 0 || sx < 0) continue;
+            g[sy * W + sx] += h[(yp + ORC_R) * PW + (xp + ORC_R)];
+        }
+    free(h);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * FoE prior energy (Eq. FOEmodel) and its gradient (Eq. FoEF).
+ * ---------------------------------------------------------------------------------------- */
+double orc_prior_energy(int nf, const double *k, const double *alpha, int H, int W, const double *u, int bc,
+                        int nthreads)
+{
+    const long N = (long)H * W;
+    double *r = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    if (!r) return NAN;
+    orc_responses(nf, k, H, W, u, bc, r, nthreads);
+    double e = 0.0;
+    for (int i = 0; i < nf; ++i) {
+        double ei = 0.0;
+        for (long p = 0; p < N; ++p) ei += orc_rho(r[(size_t)i * N + p]);
+        e += alpha[i] * ei;
+    }
+    free(r);
+    return e;
+}
+
+void orc_prior_grad(int nf, const double *k, const double *alpha, int H, int W, const double *u, int bc, double *g,
+                    int nthreads)
+{
+    const long N = (long)H * W;
+    double *r = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    if (!r) return;
+    orc_responses(nf, k, H, W, u, bc, r, nthreads);
+    for (int i = 0; i < nf; ++i)
+        for (long p = 0; p < N; ++p) r[(size_t)i * N + p] = alpha[i] * orc_rho1(r[(size_t)i * N + p]);
+    orc_adjoint(nf, k, H, W, r, bc, g, nthreads);
+    free(r);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Data terms: I-divergence <u - d log u, 1> (Eq. poissonfidelity; models 0 and 2) and the
+ * quadratic 1/2 ||u - d||^2 (Eq. overallModel; model 1), each times lambda.  0 log 0 = 0.
+ * ---------------------------------------------------------------------------------------- */
+double orc_data_energy(int model, double lambda, long n, const double *u, const double *d)
+{
+    double e = 0.0;
+    for (long i = 0; i < n; ++i) {
+        if (model == 1) {
+            e += 0.5 * (u[i] - d[i]) * (u[i] - d[i]);
+        } else {
+            if (d[i] == 0.0) e += u[i];
+            else if (u[i] <= 0.0) return INFINITY;
+            else e += u[i] - d[i] * log(u[i]);
+        }
+    }
+    return lambda * e;
+}
+
+void orc_data_grad(int model, double lambda, long n, const double *u, const double *d, double *g)
+{
+    for (long i = 0; i < n; ++i) g[i] = (model == 1) ? lambda * (u[i] - d[i]) : lambda * (1.0 - d[i] / u[i]);
+}
+
+/* Proximal map (I + tau dG)^{-1}, tl = tau * lambda:
+ *   I-divergence (Eq. subproblemGIdiv): (ut - tl + sqrt((ut - tl)^2 + 4 tl d)) / 2;
+ *   quadratic    (Eq. subproblemGL2):   (ut + tl d) / (1 + tl). */
+void orc_prox(int model, double tl, long n, const double *ut, const double *d, double *out)
+{
+    for (long i = 0; i < n; ++i) {
+        if (model == 1) out[i] = (ut[i] + tl * d[i]) / (1.0 + tl);
+        else {
+            double t = ut[i] - tl;
+            out[i] = 0.5 * (t + sqrt(t * t + 4.0 * tl * d[i]));
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * iPiano (Eq. iPianoupdate): u+ = prox_{tau G}(u - tau grad F(u) + gamma (u - u-)).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int nf;
+    const double *k;
+    const double *alpha;
+    int H, W, bc, model;
+    double lambda, tau, gamma;
+    int nthreads;
+} orc_params;
+
+double orc_energy(const orc_params *p, const double *u, const double *d)
+{
+    return orc_prior_energy(p->nf, p->k, p->alpha, p->H, p->W, u, p->bc, p->nthreads) +
+           orc_data_energy(p->model, p->lambda, (long)p->H * p->W, u, d);
+}
+
+/* Energy and gradient of the whole objective E = F + G at u. */
+double orc_energy_grad(const orc_params *p, const double *u, const double *d, double *g)
+{
+    const long N = (long)p->H * p->W;
+    double *gd = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!gd) return NAN;
+    orc_prior_grad(p->nf, p->k, p->alpha, p->H, p->W, u, p->bc, g, p->nthreads);
+    orc_data_grad(p->model, p->lambda, N, u, d, gd);
+    for (long i = 0; i < N; ++i) g[i] += gd[i];
+    free(gd);
+    return orc_energy(p, u, d);
+}
+
+/* One step: u_next from (u, u_prev). */
+void orc_ipiano_step(const orc_params *p, const double *d, const double *u, const double *u_prev, double *u_next)
+{
+    const long N = (long)p->H * p->W;
+    double *g = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ut = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!g || !ut) { free(g); free(ut); return; }
+    orc_prior_grad(p->nf, p->k, p->alpha, p->H, p->W, u, p->bc, g, p->nthreads);
+    for (long i = 0; i < N; ++i) ut[i] = u[i] - p->tau * g[i] + p->gamma * (u[i] - u_prev[i]);
+    orc_prox(p->model, p->tau * p->lambda, N, ut, d, u_next);
+    free(g);
+    free(ut);
+}
+
+/* Runs iters steps.  On entry u = u^0, u_prev = u^{-1}; on exit u = u^iters, u_prev = u^{iters-1}.
+ * energy (nullable, iters + 1 values) receives E(u^n) for n = 0..iters. */
+int orc_ipiano(const orc_params *p, const double *d, double *u, double *u_prev, int iters, double *energy)
+{
+    const long N = (long)p->H * p->W;
+    double *un = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!un) return -1;
+    if (energy) energy[0] = orc_energy(p, u, d);
+    for (int n = 0; n < iters; ++n) {
+        orc_ipiano_step(p, d, u, u_prev, un);
+        memcpy(u_prev, u, sizeof(double) * (size_t)N);
+        memcpy(u, un, sizeof(double) * (size_t)N);
+        if (energy) energy[n + 1] = orc_energy(p, u, d);
+    }
+    free(un);
+    return 0;
+}
+
+/* Whole denoiser for one image: data -> iPiano -> output.
+ *   model 0 (direct, Eq. straightforward): d = y with zeros replaced by zero_c (Sec. 3.1.1),
+ *           x = u^T;
+ *   model 1/2 (Eq. overallModel / lowcase): d = Anscombe(y), x = I_C(max(u^T, sqrt(3/2)));
+ *   model 3 (Eq. FOEscheme): 1 if peak >= 5 else 2.
+ * Initial iterates u^0 = u^{-1} = d. */
+int orc_denoise(const orc_params *p_in, const double *y, double peak, double zero_c, int iters, double *x)
+{
+    orc_params p = *p_in;
+    if (p.model == 3) p.model = (peak >= 5.0) ? 1 : 2;
+    const long N = (long)p.H * p.W;
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    double *u = (double *)malloc(sizeof(double) * (size_t)N);
+    double *up = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!d || !u || !up) { free(d); free(u); free(up); return -1; }
+    if (p.model == 0) {
+        for (long i = 0; i < N; ++i) d[i] = (y[i] == 0.0) ? zero_c : y[i];
+    } else {
+        orc_anscombe(N, y, d);
+    }
+    memcpy(u, d, sizeof(double) * (size_t)N);
+    memcpy(up, d, sizeof(double) * (size_t)N);
+    orc_ipiano(&p, d, u, up, iters, NULL);
+    if (p.model == 0) memcpy(x, u, sizeof(double) * (size_t)N);
+    else orc_inverse(N, u, x);
+    free(d);
+    free(u);
+    free(up);
+    return p.model;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Step size.  L = 2 kappa max_w sum_i alpha_i |k_i^(w)|^2 bounds the Lipschitz constant of grad F
+ * (|rho''| <= 2; the symbol maximum bounds sum_i alpha_i K_i,valid^T K_i,valid; ||P||^2 <= kappa with
+ * kappa = 4 for symmetric padding when H, W >= 6, 1 for zero padding).  The maximum is taken on an
+ * ngrid x ngrid DTFT grid.
+ * ---------------------------------------------------------------------------------------- */
+double orc_lipschitz(int nf, const double *k, const double *alpha, int bc, int ngrid)
+{
+    double best = 0.0;
+    for (int iy = 0; iy < ngrid; ++iy)
+        for (int ix = 0; ix < ngrid; ++ix) {
+            double wy = 2.0 * M_PI * iy / ngrid, wx = 2.0 * M_PI * ix / ngrid;
+            double s = 0.0;
+            for (int i = 0; i < nf; ++i) {
+                double re = 0.0, im = 0.0;
+                for (int a = -ORC_R; a <= ORC_R; ++a)
+                    for (int b = -ORC_R; b <= ORC_R; ++b) {
+                        double kv = k[(size_t)i * ORC_KK + (a + ORC_R) * ORC_KS + (b + ORC_R)];
+                        re += kv * cos(wy * a + wx * b);
+                        im -= kv * sin(wy * a + wx * b);
+                    }
+                s += alpha[i] * (re * re + im * im);
+            }
+            if (s > best) best = s;
+        }
+    return 2.0 * (bc == 1 ? 1.0 : 4.0) * best;
+}
+
+/* PSNR on the [0, 255] scale: both images are scaled by 255 / peak. */
+double orc_psnr(long n, const double *a, const double *b, double peak)
+{
+    double s = 0.0, f = 255.0 / peak;
+    for (long i = 0; i < n; ++i) {
+        double e = f * (a[i] - b[i]);
+        s += e * e;
+    }
+    double mse = s / (double)n;
+    return 10.0 * log10(255.0 * 255.0 / mse);
+}

@@ -1,0 +1,348 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test ties one oracle function to something the oracle does not compute itself: a value
+the paper states, a closed form, a library routine on a special case, an exact identity,
+a brute-force minimisation or finite differences.  A dropped term, a flipped sign, a
+transposed operand or a wrong index in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize, signal
+from scipy.stats import poisson
+
+import oracle as O
+from paper_1609_05722_gb300 import synth
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    with open(f"{GOLDEN}/{name}") as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                key, val = line.split("=")
+                vals[key.strip()] = float(val)
+    return vals
+
+
+# ----------------------------------------------------------------- transforms (Sec. 2.2, 3.1.1)
+
+def test_anscombe_zero_count_value_from_paper():
+    # Sec. 3.1.1: a zero count becomes sqrt(3/2) after the Anscombe transform.
+    g = _golden("paper_values.txt")
+    assert O.anscombe(np.array([0.0]))[0] == pytest.approx(g["anscombe_of_zero"], abs=1e-15)
+
+
+def test_inverse_anscombe_vanishes_at_zero_count_image():
+    # The inverse maps the transform of a zero count back to zero: I_C(sqrt(3/2)) = 0 exactly
+    # (3/8 + 1/4 - 11/12 + 5/12 - 1/8 = 0), so the clamp in Eq. FOEscheme's output keeps x >= 0.
+    assert abs(O.ic(math.sqrt(1.5))) < 1e-15
+    x = O.inverse(np.array([0.1, 1.0, math.sqrt(1.5)]))
+    assert np.all(x == 0.0) or abs(x).max() < 1e-15
+
+
+@pytest.mark.parametrize("lam", [0.1, 0.5, 1.0, 2.0, 4.0, 8.0, 30.0])
+def test_inverse_is_nearly_unbiased(lam):
+    # Eq. invAns approximates the exact unbiased inverse: I_C(E[2 sqrt(Y + 3/8)]) ~ lambda for
+    # Y ~ Poisson(lambda).  The expectation is summed from the pmf; 0.02 guards the closed form's
+    # approximation error (every one of its five terms matters at low counts).
+    ks = np.arange(0, int(lam * 10 + 80))
+    ea = float((poisson.pmf(ks, lam) * O.anscombe(ks.astype(float))).sum())
+    assert abs(O.ic(ea) - lam) < 0.02
+
+
+@pytest.mark.parametrize("z", [1.3, 2.0, 3.0, 7.5])
+def test_inverse_derivative_matches_finite_differences(z):
+    h = 1e-5
+    fd = (O.ic(z + h) - O.ic(z - h)) / (2 * h)
+    assert O.ic_deriv(z) == pytest.approx(fd, rel=1e-8, abs=1e-9)
+
+
+def test_inverse_large_count_asymptote():
+    # For large counts E[2 sqrt(Y + 3/8)] ~ 2 sqrt(lambda + 1/8) (Anscombe's expansion), so an
+    # unbiased inverse must approach z^2/4 - 1/8.
+    for z in (1e3, 1e4):
+        assert O.ic(z) - z * z / 4 == pytest.approx(-0.125, abs=1e-3)
+
+
+# ----------------------------------------------------------------- potential (Eq. STfunc)
+
+@pytest.mark.parametrize("z", [-3.0, -0.7, 0.0, 0.4, 1.0, 2.5, 10.0])
+def test_rho_derivatives_match_finite_differences(z):
+    h = 1e-5
+    assert O.rho1(z) == pytest.approx((O.rho(z + h) - O.rho(z - h)) / (2 * h), rel=1e-8, abs=1e-9)
+    assert O.rho2(z) == pytest.approx((O.rho1(z + h) - O.rho1(z - h)) / (2 * h), rel=1e-7, abs=1e-8)
+    assert O.rho(z) == pytest.approx(math.log(1 + z * z), rel=1e-15)
+
+
+# ----------------------------------------------------------------- padding and K (Eq. FOEmodel)
+
+@pytest.mark.parametrize("n", [7, 8, 13])
+def test_pad_index_matches_numpy_symmetric(n):
+    ref = np.pad(np.arange(n), 3, mode="symmetric")
+    got = [O.pad_index(i, n, O.BC_SYMMETRIC) for i in range(-3, n + 3)]
+    assert got == list(ref)
+    z = [O.pad_index(i, n, O.BC_ZERO) for i in range(-3, n + 3)]
+    assert z == [-1] * 3 + list(range(n)) + [-1] * 3
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (13, 17), (40, 9)])
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_responses_equal_library_convolution(bank, shape, bc):
+    # Reading of Sec. 2.3: true convolution, responses at the N image pixels on a padded image.
+    # scipy's 2-D convolution with 'symm' (edge repeated) or zero fill is the same operator.
+    k, _ = bank
+    rng = np.random.default_rng(1)
+    u = rng.uniform(0, 5, shape)
+    r = O.responses(k[:6], u, bc)
+    for i in range(6):
+        ref = signal.convolve2d(u, k[i], mode="same", boundary="symm" if bc == O.BC_SYMMETRIC else "fill")
+        np.testing.assert_allclose(r[i], ref, rtol=0, atol=1e-12)
+    # and the padded-valid form: np.pad + 'valid' convolution
+    padded = np.pad(u, 3, mode="symmetric" if bc == O.BC_SYMMETRIC else "constant")
+    np.testing.assert_allclose(r[0], signal.convolve2d(padded, k[0], mode="valid"), atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (13, 17), (7, 30)])
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_adjoint_identity(bank, shape, bc):
+    # <K u, psi> = <u, K^T psi> for the stacked operator K = (K_1; ...; K_nf), to FP64 rounding.
+    k, _ = bank
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(shape)
+    psi = rng.standard_normal((48,) + shape)
+    lhs = float((O.responses(k, u, bc) * psi).sum())
+    rhs = float((u * O.adjoint(k, psi, bc)).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-10)
+
+
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_adjoint_is_dense_transpose_on_8x8(bank, bc):
+    # Brute force: build each K_i as a dense 64x64 matrix from scipy's convolution of unit images
+    # (independent of the oracle), then K_i^T psi must equal the oracle's adjoint.
+    k, _ = bank
+    H = W = 8
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal((3, H, W))
+    expect = np.zeros(H * W)
+    for i in range(3):
+        M = np.zeros((H * W, H * W))
+        for j in range(H * W):
+            e = np.zeros(H * W)
+            e[j] = 1.0
+            M[:, j] = signal.convolve2d(e.reshape(H, W), k[i], mode="same",
+                                        boundary="symm" if bc == O.BC_SYMMETRIC else "fill").ravel()
+        expect += M.T @ psi[i].ravel()
+    np.testing.assert_allclose(O.adjoint(k[:3], psi, bc).ravel(), expect, atol=1e-12)
+
+
+def test_constant_image_has_zero_responses_under_symmetric_padding(bank):
+    k, a = bank
+    u = np.full((11, 14), 3.7)
+    assert np.abs(O.responses(k, u, O.BC_SYMMETRIC)).max() < 1e-13
+    assert np.abs(O.prior_grad(k, a, u, O.BC_SYMMETRIC)).max() < 1e-12
+
+
+# ----------------------------------------------------------------- prior gradient (Eq. FoEF)
+
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_prior_gradient_matches_finite_differences_8x8(bank, bc):
+    k, a = bank
+    rng = np.random.default_rng(4)
+    u = rng.uniform(0, 4, (8, 8))
+    g = O.prior_grad(k, a, u, bc)
+    h = 1e-5
+    fd = np.zeros_like(u)
+    for idx in np.ndindex(u.shape):
+        up, um = u.copy(), u.copy()
+        up[idx] += h
+        um[idx] -= h
+        fd[idx] = (O.prior_energy(k, a, up, bc) - O.prior_energy(k, a, um, bc)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6)
+
+
+def test_prior_gradient_matches_finite_differences_64x64_sampled(bank):
+    k, a = bank
+    rng = np.random.default_rng(5)
+    u = rng.uniform(0, 6, (64, 64))
+    g = O.prior_grad(k, a, u)
+    h = 1e-5
+    for _ in range(12):
+        idx = (int(rng.integers(64)), int(rng.integers(64)))
+        up, um = u.copy(), u.copy()
+        up[idx] += h
+        um[idx] -= h
+        fd = (O.prior_energy(k, a, up) - O.prior_energy(k, a, um)) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-5, abs=1e-5)
+
+
+def test_prior_gradient_small_signal_closed_form(bank):
+    # For equal weights a and the orthonormal zero-mean bank (sum_i k_i k_i^T = I - 11^T/49 in tap
+    # space), rho'(z) ~ 2z gives, away from the border,
+    #   grad F(eps u) / eps -> 2a (49 u - B^T B u / 49),  B = 7x7 box sum.
+    k, _ = bank
+    a = 0.8
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal((30, 30))
+    eps = 1e-5
+    g = O.prior_grad(k, np.full(48, a), eps * u, O.BC_ZERO) / eps
+    box = np.ones((7, 7))
+    Bu = signal.convolve2d(u, box, mode="same")
+    BtBu = signal.convolve2d(Bu, box, mode="same")
+    ref = 2 * a * (49 * u - BtBu / 49)
+    np.testing.assert_allclose(g[6:-6, 6:-6], ref[6:-6, 6:-6], rtol=1e-6, atol=1e-6)
+
+
+# ----------------------------------------------------------------- data terms and prox
+
+@pytest.mark.parametrize("model", [O.MODEL_DIRECT, O.MODEL_ANS_L2, O.MODEL_ANS_IDIV])
+def test_data_gradient_matches_finite_differences(model):
+    rng = np.random.default_rng(7)
+    u = rng.uniform(0.5, 5, 10)
+    d = rng.integers(0, 6, 10).astype(float)
+    g = O.data_grad(model, 1.7, u, d)
+    h = 1e-6
+    for i in range(10):
+        up, um = u.copy(), u.copy()
+        up[i] += h
+        um[i] -= h
+        fd = (O.data_energy(model, 1.7, up, d) - O.data_energy(model, 1.7, um, d)) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+@pytest.mark.parametrize("model", [O.MODEL_DIRECT, O.MODEL_ANS_L2])
+def test_prox_is_the_argmin(model):
+    # Eq. subproblemG: prox(ut) = argmin_u |u - ut|^2 / 2 + tau G(u), found by bounded 1-D search.
+    rng = np.random.default_rng(8)
+    tl = 0.37
+    for _ in range(20):
+        ut = float(rng.uniform(-2, 8))
+        d = float(rng.integers(0, 9)) if model == O.MODEL_DIRECT else float(rng.uniform(1.2, 6))
+        if model == O.MODEL_DIRECT:
+            def obj(u):
+                if u <= 0:
+                    return 0.5 * (u - ut) ** 2 + (tl * u if d == 0 else np.inf)
+                return 0.5 * (u - ut) ** 2 + tl * (u - d * math.log(u))
+            lo = 0.0
+        else:
+            def obj(u):
+                return 0.5 * (u - ut) ** 2 + tl * 0.5 * (u - d) ** 2
+            lo = -10.0
+        res = optimize.minimize_scalar(obj, bounds=(lo, 20.0), method="bounded",
+                                       options={"xatol": 1e-11, "maxiter": 2000})
+        got = O.prox(model, tl, np.array([ut]), np.array([d]))[0]
+        assert got == pytest.approx(res.x, abs=2e-6)
+
+
+def test_prox_fixed_point_at_data():
+    # With ut = d the data-term prox returns d (both forms): the reason u^0 = d is a fixed point of
+    # the data part alone.
+    d = np.array([0.0, 1.0, 3.0, 17.0])
+    assert np.allclose(O.prox(O.MODEL_DIRECT, 0.2, d, d), d, atol=1e-14)
+    assert np.allclose(O.prox(O.MODEL_ANS_L2, 0.2, d, d), d, atol=1e-14)
+
+
+# ----------------------------------------------------------------- step size
+
+def test_lipschitz_closed_form_for_equal_weights(bank):
+    # sum_i |k_i^(w)|^2 = 49 - |box^(w)|^2 / 49 for the orthonormal zero-mean bank, so
+    # max_w = 49 (reached where the box symbol vanishes) and L = 2 kappa 49 a.
+    k, _ = bank
+    a = 1.3
+    for bc, kappa in ((O.BC_SYMMETRIC, 4.0), (O.BC_ZERO, 1.0)):
+        L = O.lipschitz(k, np.full(48, a), bc, ngrid=490)  # the grid contains 2 pi j / 7
+        assert L == pytest.approx(2 * kappa * 49 * a, rel=1e-12)
+
+
+def test_lipschitz_bounds_power_iteration(bank):
+    # 2 ||sum_i alpha_i K_i^T K_i|| (power iteration on the oracle's own K, K^T) <= L.
+    k, a = bank
+    rng = np.random.default_rng(9)
+    for bc in (O.BC_SYMMETRIC, O.BC_ZERO):
+        u = rng.standard_normal((24, 24))
+        lam = 0.0
+        for _ in range(60):
+            v = O.adjoint(k, O.responses(k, u, bc) * a[:, None, None], bc)
+            lam = float(np.linalg.norm(v))
+            u = v / lam
+        assert 2 * lam <= O.lipschitz(k, a, bc, 256) * (1 + 1e-6)
+
+
+# ----------------------------------------------------------------- iPiano (Eq. iPianoupdate)
+
+def _tau(k, a, bc, gamma):
+    return 0.99 * 2 * (1 - gamma) / (O.lipschitz(k, a, bc, 256) + 2e-3)
+
+
+@pytest.mark.parametrize("model", [O.MODEL_DIRECT, O.MODEL_ANS_L2, O.MODEL_ANS_IDIV])
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_ipiano_lyapunov_decrease(bank, model, bc):
+    # With tau <= 2 (1 - gamma) / L, H(u^n, u^{n-1}) = E(u^n) + gamma / (2 tau) |u^n - u^{n-1}|^2
+    # never increases (descent lemma + prox optimality).
+    k, a = bank
+    gamma = 0.8
+    tau = _tau(k, a, bc, gamma)
+    clean = synth.clean_image(24, 20, 11)
+    y = synth.poisson_observation(clean, 4.0, 12)
+    d = y if model == O.MODEL_DIRECT else O.anscombe(y)
+    pr = O.Problem(k, a, 24, 20, bc=bc, model=model, lam=1.0, tau=tau, gamma=gamma)
+    u, up = d.copy(), d.copy()
+    Hs = []
+    for _ in range(40):
+        un = pr.step(d, u, up)
+        up, u = u, un
+        Hs.append(pr.energy(u, d) + gamma / (2 * tau) * float(((u - up) ** 2).sum()))
+    Hs = np.array(Hs)
+    assert np.all(np.diff(Hs) <= 1e-9 * np.abs(Hs[1:]))
+    assert Hs[-1] < Hs[0]
+
+
+def test_ipiano_without_inertia_decreases_energy(bank):
+    k, a = bank
+    tau = _tau(k, a, O.BC_SYMMETRIC, 0.0)
+    y = synth.poisson_observation(synth.clean_image(16, 16, 13), 8.0, 14)
+    d = O.anscombe(y)
+    pr = O.Problem(k, a, 16, 16, model=O.MODEL_ANS_L2, lam=1.0, tau=tau, gamma=0.0)
+    _, _, e = pr.ipiano(d, d, d, 30, trace=True)
+    assert np.all(np.diff(e) <= 1e-12 * np.abs(e[1:]))
+
+
+def test_ipiano_converges_to_stationary_point_8x8(bank):
+    # At convergence u = prox(u - tau grad F(u)) (first-order optimality of F + G).
+    k, a = bank
+    gamma = 0.8
+    tau = _tau(k, a, O.BC_SYMMETRIC, gamma)
+    y = synth.poisson_observation(synth.clean_image(8, 8, 15), 4.0, 16)
+    d = O.anscombe(y)
+    pr = O.Problem(k, a, 8, 8, model=O.MODEL_ANS_L2, lam=1.0, tau=tau, gamma=gamma, nthreads=1)
+    u, _ = pr.ipiano(d, d, d, 20000)
+    res = O.prox(O.MODEL_ANS_L2, tau, u - tau * O.prior_grad(k, a, u, nthreads=1), d) - u
+    assert np.abs(res).max() < 1e-9
+    # the limit is also a zero of the full gradient
+    _, g = pr.energy_grad(u, d)
+    assert np.abs(g).max() < 1e-5
+
+
+def test_denoise_model_selection_and_pipeline(bank):
+    # Eq. FOEscheme: peak >= 5 -> quadratic data term, peak < 5 -> I-divergence (Anscombe domain).
+    k, a = bank
+    y = synth.poisson_observation(synth.clean_image(12, 12, 17), 4.0, 18)
+    pr = O.Problem(k, a, 12, 12, model=O.MODEL_AUTO, lam=1.0, tau=1e-3, gamma=0.8, nthreads=1)
+    assert pr.denoise(y, 4.99, 3)[1] == O.MODEL_ANS_IDIV
+    assert pr.denoise(y, 5.0, 3)[1] == O.MODEL_ANS_L2
+    # zero iterations: the output is the inverse transform of the data (Anscombe models) or the
+    # zero-replaced data (direct model, Sec. 3.1.1)
+    x, _ = pr.denoise(y, 5.0, 0)
+    np.testing.assert_allclose(x, O.inverse(O.anscombe(y)), atol=1e-14)
+    prd = O.Problem(k, a, 12, 12, model=O.MODEL_DIRECT, lam=1.0, tau=1e-3, gamma=0.8, nthreads=1)
+    x, _ = prd.denoise(y, 4.0, 0, zero_c=0.1)
+    np.testing.assert_allclose(x, np.where(y == 0, 0.1, y), atol=0)
+
+
+def test_psnr_closed_form():
+    a = np.full(100, 2.0)
+    assert O.psnr(a + 0.1, a, 4.0) == pytest.approx(20 * math.log10(4.0 / 0.1), rel=1e-12)
