@@ -1,0 +1,371 @@
+"""Benchmark of the FoE Poisson denoiser's iPiano solve on GB300.
+
+Workload (one "step"): the 512x512 set of the paper's noise levels -- peaks {1, 2, 4, 8, 30} x
+{direct model, Anscombe quadratic model} = 10 seeded synthetic 512x512 images, 300 iterations each,
+denoised as two batches through the C ABI (foe_denoise_batch).  Metric: MPix.iter/s, i.e.
+pixels x iterations per second (whole job, inputs already in HBM; L2 flushed between steps).
+
+Printed as one JSON line on rank 0.  Extra keys: the plain-FP32 path on the same workload, the
+single-image latency, the roofline of the fused step kernel, the FP64 oracle on the host cores,
+an end-to-end figure through the public API with host buffers, and the SM clocks seen meanwhile.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16|fp32]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 512
+ITERS = 300
+PEAKS = (1.0, 2.0, 4.0, 8.0, 30.0)
+FLOP_PER_PIXEL_ITER = 2 * 2 * 48 * 49   # forward + adjoint 7x7 convolutions of 48 filters, FMA = 2 flop
+METRIC = "MPix·iter/s at 512² (TC BF16 vs FP32 plain, PSNR Δ≤0.02dB vs FP64); serve p99"
+CONFIG_NAME = "512x512 x peaks{1,2,4,8,30} x models{direct,anscombe-L2}, 300 iters, 48 7x7 filters"
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("foe_tc.cu", "foe_f32.cu", "foe_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1609_05722_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it matches the source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    e = t.get(kernel_key)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("bytes_per_launch_512x512x10")
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_sample(target_s: float = 12.0):
+    """The FP64 oracle as it stands on the host cores: one 512x512 image, iterations run until ~target_s."""
+    import oracle as O
+    from paper_1609_05722_gb300 import synth
+    k, a = synth.filter_bank()
+    y = synth.poisson_observation(synth.clean_image(H, W, 1000), 4.0, 5000)
+    d = O.anscombe(y)
+    pr = O.Problem(k, a, H, W, model=O.MODEL_ANS_L2, lam=1.0, tau=1e-3, gamma=0.8)
+    u, up = d.copy(), d.copy()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        un = pr.step(d, u, up)
+        up, u = u, un
+        n += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": H * W * n / dt / 1e6, "unit": "MPix·iter/s", "cores": O.default_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, one 512x512 image (Anscombe quadratic model), {n} iPiano iterations, "
+                      f"{O.default_threads()} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(2.0)
+    t_steps = []
+    for _ in range(args.steps):
+        s = oracle_sample(10.0)
+        vals.append(s["value"])
+        t_steps.append(H * W / (s["value"] * 1e6))
+    cb = oracle_sample(0.0)
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MPix·iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(t_steps)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME + " (oracle: bounded per-iteration sample of one image)",
+                       "step": "~10 s of FP64 oracle iterations on one 512x512 image"},
+            "cpu_baseline": {"value": v, "unit": "MPix·iter/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": "each step: FP64 oracle iterations on one 512x512 image for ~10 s"},
+            "e2e": {"value": v, "unit": "MPix·iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = rank_info()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__ as G
+    from paper_1609_05722_gb300 import build as B
+    B.build()
+    from paper_1609_05722_gb300 import foe as F
+    from paper_1609_05722_gb300 import synth
+
+    # cpu baseline first (rank 0, before any GPU work would compete for host cores)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(12.0)
+
+    k, a = synth.filter_bank()
+    ctx = F.foe_create(k, a)
+    stream = torch.cuda.current_stream()
+    ld = W
+    # 10 images: peaks x models; rank-dependent seeds (weak scaling: every rank its own images)
+    ys_host, ys, xs = [], [], []
+    for mi, model in enumerate((F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2)):
+        for pi, peak in enumerate(PEAKS):
+            seed = 1000 + 10 * pi + 100 * rank
+            y = synth.poisson_observation(synth.clean_image(H, W, seed), peak, seed + 5000).astype(np.float32)
+            yh = torch.from_numpy(y).pin_memory()
+            ys_host.append(yh)
+            ys.append(yh.to(dev))
+            xs.append(torch.empty((H, ld), dtype=torch.float32, device=dev))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+
+    def descs(xbufs, ybufs, lo, hi, iters=ITERS):
+        return [{"y": ybufs[j], "x": xbufs[j], "H": H, "W": W, "ld": ld, "peak": PEAKS[j % 5], "iters": iters}
+                for j in range(lo, hi)]
+
+    def one_step(prec, xbufs=xs, ybufs=ys):
+        for lo, model in ((0, F.FOE_MODEL_DIRECT), (5, F.FOE_MODEL_ANS_L2)):
+            F.foe_denoise_batch(ctx, descs(xbufs, ybufs, lo, lo + 5), F.SolveOpts(model=model, prec=prec),
+                                stream=stream)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            one_step(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        total = 0.0
+        F.foe_profile(ctx, True)
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        F.foe_profile(ctx, False)
+        loop_ms, launches, pix = F.foe_profile_read(ctx)
+        torch.cuda.synchronize()
+        if world > 1:
+            t = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+            dist.barrier()
+        return total, loop_ms, launches, pix
+
+    prec_main = F.FOE_PREC_BF16 if args.prec == "bf16" else F.FOE_PREC_FP32
+    try:
+        F.foe_denoise_batch(ctx, descs(xs, ys, 0, 1, 1), F.SolveOpts(prec=prec_main), stream=stream)
+    except F.FoeError as e:
+        if e.status == F.FOE_EUNSUPPORTED and prec_main == F.FOE_PREC_BF16:
+            prec_main = F.FOE_PREC_FP32  # tensor-core path not built into this library
+        else:
+            raise
+    dtype = "bf16" if prec_main == F.FOE_PREC_BF16 else "f32"
+
+    sampler = ClockSampler(local if world > 1 else 0)
+    sampler.start()
+    total_ms, loop_ms, launches, pix = timed(prec_main, args.steps, args.warmup)
+    clocks = sampler.stop()
+    pix_iters_step = 10 * H * W * ITERS
+    value = world * pix_iters_step * args.steps / (total_ms / 1e3) / 1e6
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the fused step kernel (average launch = step-loop device time / launches)
+    peaks, peak_src = measured_peaks()
+    avg_launch_s = (loop_ms / 1e3) / max(launches, 1)
+    pix_per_launch = pix / max(launches, 1)
+    if prec_main == F.FOE_PREC_BF16:
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        bound, unit, key = "tensor", "TFLOP/s", "foe_tc_step"
+    else:
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, unit, key = "alu", "TFLOP/s", "foe_f32_step"
+    achieved = pix_per_launch * FLOP_PER_PIXEL_ITER / avg_launch_s / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": ncu_traffic(key), "peak_source": f"{peak_src}"
+                + (" bf16_tflops_sustained" if bound == "tensor" else " 152 SMs x 128 FFMA/clk x 2 x sm_max_mhz"),
+                "kernel": key, "avg_launch_us": avg_launch_s * 1e6, "pixels_per_launch": pix_per_launch}
+
+    # plain FP32 path on the same workload (the comparison the metric names)
+    fp32 = None
+    if prec_main == F.FOE_PREC_BF16 and args.fp32_steps > 0:
+        t32, l32, n32, p32 = timed(F.FOE_PREC_FP32, args.fp32_steps, 1)
+        fp32 = {"value": world * pix_iters_step * args.fp32_steps / (t32 / 1e3) / 1e6, "unit": "MPix·iter/s",
+                "ms_per_step": t32 / args.fp32_steps,
+                "avg_launch_us": (l32 / 1e3) / max(n32, 1) * 1e6}
+
+    # single-image latency (one 512x512 image, 300 iterations, A2 model at peak 8)
+    xs1 = torch.empty((H, ld), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        F.foe_denoise(ctx, ys[8], xs1, H, W, ld, 8.0, F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=prec_main,
+                                                                    iters=ITERS), stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    for _ in range(3):
+        flush.zero_()
+        e0.record(stream)
+        F.foe_denoise(ctx, ys[8], xs1, H, W, ld, 8.0, F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=prec_main,
+                                                                    iters=ITERS), stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+
+    # end to end through the public API: pinned host -> device, solve, device -> pinned host, each step
+    xs_host = [torch.empty((H, ld), dtype=torch.float32).pin_memory() for _ in range(10)]
+    ybuf = [torch.empty((H, ld), dtype=torch.float32, device=dev) for _ in range(10)]
+
+    def e2e_step():
+        for j in range(10):
+            ybuf[j].copy_(ys_host[j], non_blocking=True)
+        one_step(prec_main, xbufs=xs, ybufs=ybuf)
+        for j in range(10):
+            xs_host[j].copy_(xs[j], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * pix_iters_step * args.steps / t_e2e / 1e6, "unit": "MPix·iter/s",
+           "h2d_bytes_per_step": 10 * H * W * 4, "d2h_bytes_per_step": 10 * H * ld * 4}
+
+    F.foe_destroy(ctx)
+    per_step_launches = 2 * (5 + ITERS + 5)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MPix·iter/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded images, DCT-7 filter bank)",
+                "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
+                           "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "fp32_plain": fp32, "single_image_ms": float(np.median(lat)),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * foe.h: C ABI of the GB300 FoE Poisson denoiser.
+ *
+ * Method: Feng, Qiao, Chen, "Poisson Noise Reduction with Higher-order Natural Image Prior Model"
+ * (arXiv:1609.05722).  Each solve minimises
+ *
+ *     E(u) = sum_i alpha_i sum_p rho((k_i * u)_p) + D(u),   rho(z) = log(1 + z^2)   (Eq. FOEmodel, STfunc)
+ *
+ * with iPiano (Eq. iPianoupdate): u+ = prox_{tau D}(u - tau grad F(u) + gamma (u - u-)),
+ * grad F(u) = sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF).  Three data terms D:
+ *   FOE_MODEL_DIRECT    lambda <x - y log x, 1> on the counts y           (Eq. straightforward, prox Eq. subproblemGIdiv)
+ *   FOE_MODEL_ANS_L2    lambda/2 ||u - v||^2, v = 2 sqrt(y + 3/8)         (Eq. overallModel, prox Eq. subproblemGL2)
+ *   FOE_MODEL_ANS_IDIV  lambda <u - v log u, 1> in the Anscombe domain    (Eq. lowcase)
+ *   FOE_MODEL_AUTO      ANS_L2 if peak >= 5 else ANS_IDIV                 (Eq. FOEscheme)
+ * The Anscombe models return x = I_C(max(u, sqrt(3/2))) (Eq. invAns); the direct model returns u.
+ *
+ * Conventions
+ *   - Images are FP32, row-major, H rows x W columns, row pitch ld floats (ld >= W, ld % 4 == 0),
+ *     device-resident unless a parameter says "host".  H, W >= 7.
+ *   - Filters are 7x7 convolution kernels: filters[i*49 + (a+3)*7 + (b+3)] = k_i(a, b), a, b in -3..3,
+ *     (k * u)_p = sum_{a,b} k(a, b) u(p - (a, b)).  Responses exist at the image pixels only, on the
+ *     image padded by P: FOE_BC_SYMMETRIC = half-sample reflection (edge repeated), FOE_BC_ZERO = zeros.
+ *     The gradient is the exact adjoint P^T K_valid^T.
+ *   - Ownership: the caller owns every image buffer; the context owns its filter copies, its cached
+ *     step size and its workspace (grown on demand with cudaMalloc; never shrunk until foe_destroy).
+ *   - Execution: calls are stream-ordered on the given cudaStream_t (NULL = legacy default stream).
+ *     Results written to host pointers (energies, reports) synchronise that stream first.
+ *   - Errors: no call aborts or throws.  Each returns a foe_status; foe_last_error(ctx) gives text.
+ *     Argument errors are detected on the host before any device work (FOE_EINVAL).
+ *   - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef FOE_H
+#define FOE_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define FOE_API __attribute__((visibility("default")))
+#else
+#define FOE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FOE_OK = 0,
+    FOE_EINVAL = 1,       /* bad argument (detected on the host, nothing launched) */
+    FOE_ENOMEM = 2,       /* device or host allocation failed */
+    FOE_ECUDA = 3,        /* a CUDA runtime call failed; the text names it */
+    FOE_ENONFINITE = 4,   /* a non-finite value was produced */
+    FOE_ETIMEOUT = 5,     /* a bounded device-side wait expired */
+    FOE_EBUSY = 6,        /* resource in use */
+    FOE_EUNSUPPORTED = 7  /* option not implemented for this combination */
+} foe_status;
+
+typedef enum { FOE_MODEL_DIRECT = 0, FOE_MODEL_ANS_L2 = 1, FOE_MODEL_ANS_IDIV = 2, FOE_MODEL_AUTO = 3 } foe_model;
+
+/* Arithmetic of the 96 convolutions per iteration.  State, data term and prox are always FP32
+ * (the iterate is held as an unevaluated FP32 pair hi + lo). */
+typedef enum { FOE_PREC_FP32 = 0, FOE_PREC_TF32 = 1, FOE_PREC_BF16 = 2 } foe_precision;
+
+typedef enum { FOE_BC_SYMMETRIC = 0, FOE_BC_ZERO = 1 } foe_bc;
+
+typedef enum { FOE_STEP_FIXED = 0, FOE_STEP_BACKTRACK = 1 } foe_step_mode;
+
+typedef struct foe_ctx foe_ctx;
+
+/* FoE prior (Eq. FOEmodel): nf filters of ksize x ksize and their weights (host memory, copied). */
+typedef struct {
+    int nf;               /* 1..48 */
+    int ksize;            /* must be 7 */
+    const float *filters; /* host, [nf][49] convolution kernels as described above */
+    const float *alpha;   /* host, [nf], > 0 (the weights themselves, i.e. e^{alpha} of Eq. learningmodel) */
+} foe_prior;
+
+typedef struct {
+    foe_model model;
+    float lambda;         /* data-term weight, > 0 */
+    float gamma;          /* inertia, 0 <= gamma < 1 */
+    float tau;            /* step size; 0 = the context's default for (bc, gamma) */
+    float tol;            /* reserved (0): iterations always run to `iters` */
+    int iters;            /* >= 0 */
+    foe_step_mode step;   /* FOE_STEP_FIXED only */
+    foe_bc bc;
+    foe_precision prec;
+    float zero_c;         /* direct model: zero counts are replaced by zero_c (Sec. 3.1.1), >= 0 */
+} foe_solve_opts;
+
+typedef struct {
+    int iters_done;
+    int model_used;       /* resolved foe_model (never AUTO) */
+    float tau_used;
+    foe_status status;
+} foe_report;
+
+/* One image of a batch (foe_denoise_batch). */
+typedef struct {
+    const float *y;       /* device, noisy counts, H x W, pitch ld */
+    float *x;             /* device, output, H x W, pitch ld (may alias y) */
+    int H, W, ld;
+    float peak;           /* used for FOE_MODEL_AUTO */
+    int iters;            /* per-image iteration budget, >= 0 */
+} foe_image_desc;
+
+/* Fills *opts with the defaults: AUTO model, lambda 1, gamma 0.8, tau 0 (auto), 300 iterations,
+ * fixed steps, symmetric padding, BF16 convolutions, zero_c 0. */
+FOE_API foe_status foe_default_opts(foe_solve_opts *opts);
+
+/* Creates a context for one prior: validates it, copies the filters to the device and precomputes
+ * the Lipschitz bound of grad F used for the default step size.  Needs a current CUDA device. */
+FOE_API foe_status foe_create(const foe_prior *prior, foe_ctx **out);
+
+/* Releases the context and its device memory.  NULL is ignored.  The caller must make sure no
+ * work that uses the context is still running. */
+FOE_API void foe_destroy(foe_ctx *ctx);
+
+/* Host-only: the step size used when opts.tau == 0.
+ *   L   = 2 kappa max_w sum_i alpha_i |k_i^(w)|^2  (kappa = 4 symmetric, 1 zero padding; the maximum
+ *         over a 512 x 512 DTFT grid, FP64), a bound on the Lipschitz constant of grad F
+ *         (|rho''| <= 2, Sec. 2.5.2);
+ *   tau = 0.99 * 2 (1 - gamma) / (L + 2e-3), inside iPiano's step condition tau < 2 (1 - gamma) / L.
+ * Either output pointer may be NULL. */
+FOE_API foe_status foe_step_size(const foe_ctx *ctx, foe_bc bc, float gamma, float *tau_out, double *lipschitz_out);
+
+/* Host-only, needs no device: the Lipschitz bound L above for a prior that has no context yet. */
+FOE_API foe_status foe_prior_lipschitz(const foe_prior *prior, foe_bc bc, double *lipschitz_out);
+
+/* Denoises one image (steps a1-a10 of the solve): data term from y, iPiano iterations, output map.
+ *   y    device, noisy counts (non-negative integers stored as FP32), H x W, pitch ld
+ *   x    device, output in the intensity domain, H x W, pitch ld (may alias y)
+ *   peak the noise level (max of the clean image, Sec. 2.1); only FOE_MODEL_AUTO reads it
+ *   rep  host, nullable; if given, the stream is synchronised and the report filled */
+FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
+                       const foe_solve_opts *opts, void *stream, foe_report *rep);
+
+/* Denoises n independent images of mixed sizes and iteration budgets in one stream-ordered pass:
+ * every iteration advances all images whose budget is not yet spent, in one launch over the tiles
+ * of all of them.  opts->iters is ignored (each desc carries its own). */
+FOE_API foe_status foe_denoise_batch(foe_ctx *ctx, const foe_image_desc *descs, int n, const foe_solve_opts *opts,
+                             void *stream);
+
+/* Energy and gradient of E = F + D at u (Eq. FOEmodel + the model's data term; gradient Eq. FoEF plus
+ * grad D).  model must be DIRECT, ANS_L2 or ANS_IDIV; data is y (DIRECT) or v (Anscombe models).
+ *   energy_host  host, nullable: E(u), accumulated in FP64 on the device; synchronises the stream
+ *   grad         device, nullable: H x W with pitch ld */
+FOE_API foe_status foe_energy_grad(foe_ctx *ctx, const float *u, const float *data, int H, int W, int ld, foe_model model,
+                           float lambda, foe_bc bc, foe_precision prec, double *energy_host, float *grad,
+                           void *stream);
+
+/* One iPiano step (Eq. iPianoupdate) on a state given explicitly, for callers that drive the loop:
+ *   u_hi, u_lo   device, the iterate u^n = u_hi + u_lo (u_lo may be NULL = zeros; written if not NULL)
+ *   delta        device, u^n - u^{n-1} (read, then overwritten with u^{n+1} - u^n)
+ *   d            device, the data term (y for DIRECT, v for the Anscombe models)
+ *   u_next_hi    device, receives the high part of u^{n+1}; must not alias u_hi
+ * model must not be AUTO.  All images H x W with pitch ld. */
+FOE_API foe_status foe_ipiano_step(foe_ctx *ctx, const float *u_hi, float *u_lo, float *delta, const float *d,
+                           float *u_next_hi, int H, int W, int ld, foe_model model, float lambda, float tau,
+                           float gamma, foe_bc bc, foe_precision prec, void *stream);
+
+/* Elementwise maps on n-element device arrays.
+ *   foe_anscombe: v = 2 sqrt(y + 3/8)            (Eq. Anscombetransform)
+ *   foe_inverse:  x = I_C(max(z, sqrt(3/2)))     (Eq. invAns) */
+FOE_API foe_status foe_anscombe(const float *y, float *v, long n, void *stream);
+FOE_API foe_status foe_inverse(const float *z, float *x, long n, void *stream);
+
+/* Step-kernel timing (tracing aid).  foe_profile(ctx, 1) clears the counters and starts recording a
+ * CUDA event pair around every iteration loop that foe_denoise / foe_denoise_batch enqueue (on the
+ * caller's stream); foe_profile(ctx, 0) stops recording.  foe_profile_read waits for the recorded
+ * events and returns, since the last foe_profile(ctx, 1): the summed device time of those loops in
+ * ms, the number of step-kernel launches inside them, and the pixel-iterations they processed.
+ * Any output pointer may be NULL. */
+FOE_API foe_status foe_profile(foe_ctx *ctx, int enable);
+FOE_API foe_status foe_profile_read(foe_ctx *ctx, double *loop_ms, long *launches, double *pixel_iters);
+
+FOE_API const char *foe_status_string(foe_status s);
+
+/* Last error text of the context (never NULL). */
+FOE_API const char *foe_last_error(const foe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOE_H */

@@ -1,0 +1,174 @@
+// Device-side definitions shared by the FoE kernels: launch descriptors, padding, the compensated
+// FP32 iterate update and the pointwise proximal maps.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace foe {
+
+constexpr int kNF = 48;     // filters (Sec. 2.5.3: 48 filters of 7x7)
+constexpr int kKS = 7;      // filter side
+constexpr int kKK = 49;     // taps
+constexpr int kR = 3;       // filter radius
+constexpr int kMaxBatch = 64;
+
+enum Model : int { kDirect = 0, kAnsL2 = 1, kAnsIdiv = 2 };
+enum Bc : int { kSymmetric = 0, kZero = 1 };
+enum Mode : int { kStep = 0, kGrad = 1, kEnergy = 2 };
+
+// Constants of one iPiano step (Eq. iPianoupdate) for one image.  Products that must stay
+// accurate (tau*lambda and the quadratic prox weights) are carried as FP32 pairs hi + lo,
+// computed on the host in FP64.
+struct StepConsts {
+    float tau, gamma, lambda;
+    float c_hi, c_lo;          // c = tau * lambda
+    float a1_hi, a1_lo;        // 1 / (1 + c)        (quadratic prox, Eq. subproblemGL2)
+    float a2_hi, a2_lo;        // c / (1 + c)
+};
+
+// One image of a launch.  u_hi is double-buffered: a launch reads u_hi[parity] (with halos) and
+// writes u_hi[parity ^ 1]; u_lo and delta are private to each pixel and updated in place.
+struct ImgDesc {
+    float *u_hi[2];
+    float *u_lo;               // may be null in kGrad / kEnergy modes
+    float *delta;              // u^n - u^{n-1}
+    const float *d;            // data term: y (direct) or v (Anscombe models)
+    float *out;                // kGrad: gradient; unused otherwise
+    int H, W, ld;
+    int tiles_x;
+    int model;
+    StepConsts sc;
+};
+
+struct LaunchArgs {
+    int nimg;
+    int parity;
+    int bc;
+    int nchunks;               // ceil(nf / 8)
+    const float *wts;          // device [48][49], correlation form w_i(a, b) = k_i(-a, -b)
+    const float *alpha;        // device [48]
+    double *partials;          // kEnergy: one FP64 partial per tile
+    int tile_prefix[kMaxBatch + 1];
+    ImgDesc img[kMaxBatch];
+};
+
+// Half-sample symmetric padding (edge repeated), any overshoot; -1 for zero padding outside.
+__host__ __device__ inline int pad_index(int i, int n, int bc)
+{
+    if (bc == kZero) return (i >= 0 && i < n) ? i : -1;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -1 - i;
+        if (i >= n) i = 2 * n - 1 - i;
+    }
+    return i;
+}
+
+// ---- error-free transformations on FP32 (Knuth two-sum, Dekker fast two-sum, FMA two-product) ----
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (ah + al) + (bh + bl)
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &rh, float &rl)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(s, e, rh, rl);
+}
+
+// (ah + al) * (bh + bl), low-order cross term bl*al dropped
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &rh, float &rl)
+{
+    float p, e;
+    two_prod(ah, bh, p, e);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    fast_two_sum(p, e, rh, rl);
+}
+
+// iPiano update of one pixel.  g = grad F(u^n) (FP32); the iterate is u = uh + ul, delta = u^n - u^{n-1}.
+//   u~    = u - tau g + gamma delta                               (forward + inertial step)
+//   u^{n+1} = prox(u~): quadratic (u~ + c d) / (1 + c)            (Eq. subproblemGL2)
+//                      I-divergence (t + sqrt(t^2 + 4 c d)) / 2, t = u~ - c   (Eq. subproblemGIdiv)
+// All in FP32 pair arithmetic so that rounding does not accumulate over hundreds of iterations.
+__device__ __forceinline__ void ipiano_update(float g, float uh, float ul, float delta, float d, int model,
+                                              const StepConsts &sc, float &nh, float &nl, float &ndelta)
+{
+    const float s = __fmaf_rn(sc.gamma, delta, -__fmul_rn(sc.tau, g));
+    float th, tl;
+    two_sum(uh, s, th, tl);
+    tl = __fadd_rn(tl, ul);
+    fast_two_sum(th, tl, th, tl);
+    float ph, pl;
+    if (model == kAnsL2) {
+        float xh, xl, yh, yl;
+        df_mul(th, tl, sc.a1_hi, sc.a1_lo, xh, xl);
+        df_mul(d, 0.0f, sc.a2_hi, sc.a2_lo, yh, yl);
+        df_add(xh, xl, yh, yl, ph, pl);
+    } else {
+        float qh, ql, sh, sl, mh, ml;
+        df_add(th, tl, -sc.c_hi, -sc.c_lo, qh, ql);            // t = u~ - c
+        df_mul(qh, ql, qh, ql, sh, sl);                        // t^2
+        df_mul(4.0f * sc.c_hi, 4.0f * sc.c_lo, d, 0.0f, mh, ml);  // 4 c d
+        float zh, zl;
+        df_add(sh, sl, mh, ml, zh, zl);                        // t^2 + 4 c d >= 0
+        float rh = 0.0f, rl = 0.0f;
+        if (zh > 0.0f) {
+            rh = __fsqrt_rn(zh);
+            rl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, zh), zl), __fmul_rn(2.0f, rh));
+        }
+        df_add(qh, ql, rh, rl, ph, pl);
+        ph *= 0.5f;
+        pl *= 0.5f;
+    }
+    float dh, dl;
+    df_add(ph, pl, -uh, -ul, dh, dl);
+    nh = ph;
+    nl = pl;
+    ndelta = __fadd_rn(dh, dl);
+}
+
+// Gradient of the data term, FP32: lambda (1 - d / u) for the I-divergence forms, lambda (u - d) for the quadratic one.
+__device__ __forceinline__ float data_grad(float u, float d, int model, float lambda)
+{
+    return model == kAnsL2 ? lambda * (u - d) : lambda * (1.0f - d / u);
+}
+
+// Data term energy of one pixel in FP64 (0 log 0 = 0).
+__device__ __forceinline__ double data_energy(float u, float d, int model, float lambda)
+{
+    const double ud = u, dd = d;
+    if (model == kAnsL2) return 0.5 * lambda * (ud - dd) * (ud - dd);
+    if (dd == 0.0) return lambda * ud;
+    return lambda * (ud - dd * log(ud));
+}
+
+// Image index of a flat tile index (binary search over the launch's tile prefix).
+__device__ __forceinline__ int tile_image(const LaunchArgs &a, int tile)
+{
+    int lo = 0, hi = a.nimg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.tile_prefix[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace foe

@@ -1,0 +1,238 @@
+"""Thin Python binding of the C ABI in ``include/foe.h`` (ctypes; argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device buffers are passed as
+objects with ``data_ptr()`` (torch tensors) or as integer addresses; streams as a
+``torch.cuda.Stream``, a raw handle or ``None`` (torch's current stream when torch is loaded,
+else the legacy default stream).  All arithmetic runs in the CUDA library: if ``libfoe.so``
+is missing, every call raises instead of computing anything on the host.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfoe.so")
+
+FOE_OK, FOE_EINVAL, FOE_ENOMEM, FOE_ECUDA, FOE_ENONFINITE, FOE_ETIMEOUT, FOE_EBUSY, FOE_EUNSUPPORTED = range(8)
+FOE_MODEL_DIRECT, FOE_MODEL_ANS_L2, FOE_MODEL_ANS_IDIV, FOE_MODEL_AUTO = range(4)
+FOE_PREC_FP32, FOE_PREC_TF32, FOE_PREC_BF16 = range(3)
+FOE_BC_SYMMETRIC, FOE_BC_ZERO = range(2)
+FOE_STEP_FIXED, FOE_STEP_BACKTRACK = range(2)
+
+_fp = C.POINTER(C.c_float)
+
+
+class foe_prior(C.Structure):
+    _fields_ = [("nf", C.c_int), ("ksize", C.c_int), ("filters", _fp), ("alpha", _fp)]
+
+
+class foe_solve_opts(C.Structure):
+    _fields_ = [("model", C.c_int), ("lam", C.c_float), ("gamma", C.c_float), ("tau", C.c_float),
+                ("tol", C.c_float), ("iters", C.c_int), ("step", C.c_int), ("bc", C.c_int),
+                ("prec", C.c_int), ("zero_c", C.c_float)]
+
+
+class foe_report(C.Structure):
+    _fields_ = [("iters_done", C.c_int), ("model_used", C.c_int), ("tau_used", C.c_float), ("status", C.c_int)]
+
+
+class foe_image_desc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("x", C.c_void_p), ("H", C.c_int), ("W", C.c_int), ("ld", C.c_int),
+                ("peak", C.c_float), ("iters", C.c_int)]
+
+
+class FoeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libfoe.so; raises if it has not been built (there is no host fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run paper_1609_05722_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, i, f, d = C.c_void_p, C.c_int, C.c_float, C.c_double
+        sig = {
+            "foe_default_opts": (i, [C.POINTER(foe_solve_opts)]),
+            "foe_create": (i, [C.POINTER(foe_prior), C.POINTER(vp)]),
+            "foe_destroy": (None, [vp]),
+            "foe_step_size": (i, [vp, i, f, C.POINTER(f), C.POINTER(d)]),
+            "foe_prior_lipschitz": (i, [C.POINTER(foe_prior), i, C.POINTER(d)]),
+            "foe_denoise": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
+            "foe_denoise_batch": (i, [vp, C.POINTER(foe_image_desc), i, C.POINTER(foe_solve_opts), vp]),
+            "foe_energy_grad": (i, [vp, vp, vp, i, i, i, i, f, i, i, C.POINTER(d), vp, vp]),
+            "foe_ipiano_step": (i, [vp, vp, vp, vp, vp, vp, i, i, i, i, f, f, f, i, i, vp]),
+            "foe_anscombe": (i, [vp, vp, C.c_long, vp]),
+            "foe_inverse": (i, [vp, vp, C.c_long, vp]),
+            "foe_profile": (i, [vp, i]),
+            "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
+            "foe_status_string": (C.c_char_p, [i]),
+            "foe_last_error": (C.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import sys
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(status: int, ctx=None, what: str = ""):
+    if status != FOE_OK:
+        text = lib().foe_status_string(status).decode()
+        if ctx is not None:
+            text += ": " + lib().foe_last_error(ctx).decode()
+        raise FoeError(status, f"{what}: {text}" if what else text)
+
+
+def foe_status_string(status: int) -> str:
+    return lib().foe_status_string(status).decode()
+
+
+def foe_last_error(ctx) -> str:
+    return lib().foe_last_error(ctx).decode()
+
+
+@dataclass
+class SolveOpts:
+    """Python mirror of foe_solve_opts (defaults of foe_default_opts)."""
+    model: int = FOE_MODEL_AUTO
+    lam: float = 1.0
+    gamma: float = 0.8
+    tau: float = 0.0
+    tol: float = 0.0
+    iters: int = 300
+    step: int = FOE_STEP_FIXED
+    bc: int = FOE_BC_SYMMETRIC
+    prec: int = FOE_PREC_BF16
+    zero_c: float = 0.0
+
+    def c(self) -> foe_solve_opts:
+        return foe_solve_opts(self.model, self.lam, self.gamma, self.tau, self.tol, self.iters, self.step,
+                              self.bc, self.prec, self.zero_c)
+
+
+def foe_default_opts() -> SolveOpts:
+    o = foe_solve_opts()
+    _check(lib().foe_default_opts(C.byref(o)))
+    return SolveOpts(o.model, o.lam, o.gamma, o.tau, o.tol, o.iters, o.step, o.bc, o.prec, o.zero_c)
+
+
+def _prior(filters, alpha):
+    k = np.asarray(filters, dtype=np.float32)
+    ks = k.shape[-1] if k.ndim == 3 else 7
+    k = np.ascontiguousarray(k.reshape(k.shape[0], -1))
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float32).ravel())
+    p = foe_prior(k.shape[0], ks, k.ctypes.data_as(_fp), a.ctypes.data_as(_fp))
+    return p, (k, a)
+
+
+def foe_prior_lipschitz(filters, alpha, bc: int = FOE_BC_SYMMETRIC) -> float:
+    p, _keep = _prior(filters, alpha)
+    out = C.c_double()
+    _check(lib().foe_prior_lipschitz(C.byref(p), bc, C.byref(out)), what="foe_prior_lipschitz")
+    return out.value
+
+
+def foe_create(filters, alpha) -> int:
+    """filters: (nf, 7, 7) convolution kernels k_i(a, b); alpha: (nf,) positive weights."""
+    p, _keep = _prior(filters, alpha)
+    h = C.c_void_p()
+    _check(lib().foe_create(C.byref(p), C.byref(h)), what="foe_create")
+    return h.value
+
+
+def foe_destroy(ctx) -> None:
+    if ctx:
+        lib().foe_destroy(ctx)
+
+
+def foe_step_size(ctx, bc: int = FOE_BC_SYMMETRIC, gamma: float = 0.8) -> tuple[float, float]:
+    t, L = C.c_float(), C.c_double()
+    _check(lib().foe_step_size(ctx, bc, gamma, C.byref(t), C.byref(L)), ctx, "foe_step_size")
+    return t.value, L.value
+
+
+def foe_denoise(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts | None = None, stream=None,
+                report: bool = False):
+    o = (opts or SolveOpts()).c()
+    rep = foe_report()
+    _check(lib().foe_denoise(ctx, _ptr(y), _ptr(x), H, W, ld, peak, C.byref(o), _stream(stream),
+                             C.byref(rep) if report else None), ctx, "foe_denoise")
+    if report:
+        return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
+                "status": rep.status}
+    return None
+
+
+def foe_denoise_batch(ctx, descs: list[dict], opts: SolveOpts | None = None, stream=None) -> None:
+    """descs: dicts with y, x (device buffers), H, W, ld, peak, iters."""
+    arr = (foe_image_desc * len(descs))()
+    for j, d in enumerate(descs):
+        arr[j] = foe_image_desc(_ptr(d["y"]), _ptr(d["x"]), d["H"], d["W"], d["ld"], d["peak"], d["iters"])
+    o = (opts or SolveOpts()).c()
+    _check(lib().foe_denoise_batch(ctx, arr, len(descs), C.byref(o), _stream(stream)), ctx, "foe_denoise_batch")
+
+
+def foe_energy_grad(ctx, u, data, H: int, W: int, ld: int, model: int, lam: float, bc: int = FOE_BC_SYMMETRIC,
+                    prec: int = FOE_PREC_FP32, grad=None, energy: bool = True, stream=None):
+    e = C.c_double()
+    _check(lib().foe_energy_grad(ctx, _ptr(u), _ptr(data), H, W, ld, model, lam, bc, prec,
+                                 C.byref(e) if energy else None, _ptr(grad), _stream(stream)), ctx, "foe_energy_grad")
+    return e.value if energy else None
+
+
+def foe_ipiano_step(ctx, u_hi, u_lo, delta, d, u_next_hi, H: int, W: int, ld: int, model: int, lam: float,
+                    tau: float, gamma: float, bc: int = FOE_BC_SYMMETRIC, prec: int = FOE_PREC_FP32,
+                    stream=None) -> None:
+    _check(lib().foe_ipiano_step(ctx, _ptr(u_hi), _ptr(u_lo), _ptr(delta), _ptr(d), _ptr(u_next_hi), H, W, ld,
+                                 model, lam, tau, gamma, bc, prec, _stream(stream)), ctx, "foe_ipiano_step")
+
+
+def foe_anscombe(y, v, n: int, stream=None) -> None:
+    _check(lib().foe_anscombe(_ptr(y), _ptr(v), n, _stream(stream)), what="foe_anscombe")
+
+
+def foe_inverse(z, x, n: int, stream=None) -> None:
+    _check(lib().foe_inverse(_ptr(z), _ptr(x), n, _stream(stream)), what="foe_inverse")
+
+
+def foe_profile(ctx, enable: bool = True) -> None:
+    _check(lib().foe_profile(ctx, 1 if enable else 0), ctx, "foe_profile")
+
+
+def foe_profile_read(ctx) -> tuple[float, int, float]:
+    """(summed step-loop device time in ms, step-kernel launches, pixel-iterations) since foe_profile(ctx, True)."""
+    ms, n, px = C.c_double(), C.c_long(), C.c_double()
+    _check(lib().foe_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(px)), ctx, "foe_profile_read")
+    return ms.value, n.value, px.value
