@@ -1,5 +1,6 @@
 // C ABI of the FoE denoiser: argument checks, context and workspace, step size, launch sequencing.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -20,6 +21,7 @@ struct foe_ctx {
     double symbol_max = 0.0;                // max_w sum_i alpha_i |k_i^(w)|^2
     float *d_wts = nullptr;                 // device [48][49], correlation orientation
     float *d_alpha = nullptr;               // device [48]
+    void *d_tcops = nullptr;                // device, bf16 operand images of the tensor-core kernel (12 KB)
     void *ws = nullptr;
     size_t ws_bytes = 0;
     double *d_partials = nullptr;
@@ -87,6 +89,34 @@ double symbol_max(const float *k, const float *alpha, int nf, int n)
             best = std::max(best, s);
         }
     return best;
+}
+
+uint16_t f32_to_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even (inputs are finite)
+    return (uint16_t)(u >> 16);
+}
+
+// bf16 operand images of the tensor-core kernel, from correlation weights w[48][49] and alpha:
+//   forward B  [tap row a (8)][filter (48)][tap col b (8)] = w_f(a, b)          (0 for a or b = 7)
+//   adjoint B  [filter group (6)][tap 8a+b (64)][filter in group (8)] = 2 alpha_f w_f(a, b)
+std::vector<uint16_t> tc_operands(const float *w, const float *alpha)
+{
+    std::vector<uint16_t> out(8 * 48 * 8 + 6 * 64 * 8, 0);
+    for (int a = 0; a < 8; ++a)
+        for (int f = 0; f < 48; ++f)
+            for (int b = 0; b < 8; ++b)
+                out[(a * 48 + f) * 8 + b] = (a < 7 && b < 7) ? f32_to_bf16(w[f * foe::kKK + a * 7 + b]) : 0;
+    uint16_t *adj = out.data() + 8 * 48 * 8;
+    for (int g = 0; g < 6; ++g)
+        for (int n = 0; n < 64; ++n)
+            for (int e = 0; e < 8; ++e) {
+                const int f = 8 * g + e, a = n / 8, b = n % 8;
+                adj[(g * 64 + n) * 8 + e] = (a < 7 && b < 7) ? f32_to_bf16(2.0f * alpha[f] * w[f * foe::kKK + a * 7 + b]) : 0;
+            }
+    return out;
 }
 
 foe_status check_prior(const foe_prior *p)
@@ -175,6 +205,7 @@ void args_begin(foe_ctx *c, int bc)
     A.wts = c->d_wts;
     A.alpha = c->d_alpha;
     A.partials = c->d_partials;
+    A.tcops = c->d_tcops;
     A.tile_prefix[0] = 0;
 }
 
@@ -329,8 +360,11 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         foe_destroy(c);
         return s;
     };
+    const std::vector<uint16_t> ops = tc_operands(w, c->alpha);
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_wts, sizeof(w))) || (e = cudaMalloc(&c->d_alpha, sizeof(c->alpha))) ||
+        (e = cudaMalloc(&c->d_tcops, ops.size() * sizeof(uint16_t))) ||
+        (e = cudaMemcpy(c->d_tcops, ops.data(), ops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice)) ||
         (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) ||
         (e = cudaMemcpy(c->d_wts, w, sizeof(w), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
@@ -348,6 +382,7 @@ void foe_destroy(foe_ctx *c)
     prof_clear(c);
     cudaFree(c->d_wts);
     cudaFree(c->d_alpha);
+    cudaFree(c->d_tcops);
     cudaFree(c->d_energy);
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
@@ -406,11 +441,18 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
     FOE_CUDA(c, foe::launch_output(uf, sl.ul, H, W, ld, ld, model, x, s));
     if (rep) {
+        int dev_status = 0;
+        FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaStreamSynchronize(s));
         rep->iters_done = o->iters;
         rep->model_used = model;
         rep->tau_used = tau;
-        rep->status = FOE_OK;
+        rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
+        if (dev_status) {
+            FOE_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_err(c, "a device-side wait expired during the solve");
+            return (foe_status)dev_status;
+        }
     }
     return FOE_OK;
 }

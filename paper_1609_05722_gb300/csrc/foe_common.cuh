@@ -49,6 +49,7 @@ struct LaunchArgs {
     const float *wts;          // device [48][49], correlation form w_i(a, b) = k_i(-a, -b)
     const float *alpha;        // device [48]
     double *partials;          // kEnergy: one FP64 partial per tile
+    const void *tcops;         // tensor-core operand images (bf16): forward filters, then adjoint filters
     int tile_prefix[kMaxBatch + 1];
     ImgDesc img[kMaxBatch];
 };

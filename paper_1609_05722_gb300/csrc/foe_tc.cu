@@ -1,10 +1,421 @@
-// Tensor-core (tcgen05) fused FoE tile kernel: placeholder until the kernel lands.
+// Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, FP32 accumulators in
+// tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
+//
+// One CTA owns a 26x26 output tile.  The prior gradient sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF)
+// needs the responses on the tile plus a 3-pixel ring: a 32x32 response region, processed as 8
+// M-tiles of 128 response pixels (4 rows of 32).
+//
+//   forward   R[m][i]  = sum_k A[m][k] Wf[i][k]        M=128, N=48 filters, K=64 (8x8 taps, 49 used)
+//             A is never materialised as an im2col matrix: E holds, for every input position, the 8
+//             horizontally adjacent bf16 values u(y, x..x+7), so the K-slice "tap rows 2s, 2s+1" of
+//             the 128 pixels of an M-tile is two shifted, regularly strided views of E that one shared
+//             memory descriptor addresses (leading offset = one E row, stride = 8 entries).
+//   expert    psi[m][i] = rho'(R) / 2 = R / (1 + R^2), zero outside the image; 2 alpha_i lives in Wa.
+//   adjoint   Z[m][n]  = sum_i Psi[m][i] Wa[n][i]      M=128, N=64 taps (8a+b), K=48 filters
+//             g(q) = sum_{a,b} Z[q - (a-3, b-3)][8a+b]: the horizontal part of this col2im is done
+//             with warp shuffles (a warp holds one response row of 32 pixels), the vertical part
+//             through shared memory.
+//
+// Roles: warps 0-3 move data between tensor memory and registers (warp w reads TMEM lanes 32w..32w+31,
+// i.e. response row 4t+w of M-tile t) and do the pointwise work; one thread of warp 4 issues the MMAs.
+// R and Z are double-buffered in tensor memory and Psi in shared memory, so the forward MMA of M-tile
+// t+1 and the adjoint MMA of tile t overlap the epilogue of tile t.  Every mbarrier wait is bounded:
+// on expiry the CTA records FOE_ETIMEOUT in *status, drains its MMAs, frees its tensor memory and
+// finishes without further waits.
+//
+// BF16 range: filters are zero-mean, so K(u - c) = K u for any constant c (the padded image of a
+// constant is constant under symmetric padding; under zero padding the padded zeros are shifted by -c
+// too).  The tile mean is subtracted before rounding u to BF16.
+#include <cstdint>
+
+#include "foe_common.cuh"
 #include "foe_kernels.h"
 
 namespace foe {
-int tc_tile_h() { return 32; }
-int tc_tile_w() { return 26; }
-size_t tc_smem_bytes() { return 0; }
-cudaError_t tc_setup() { return cudaSuccess; }
-cudaError_t tc_launch(const LaunchArgs &, int, int *, cudaStream_t) { return cudaErrorNotSupported; }
+
+namespace {
+
+constexpr int TO = 26;                 // output tile side
+constexpr int RS = TO + 6;             // response region side = 32 = warp width
+constexpr int NMT = RS / 4;            // M-tiles per CTA
+constexpr int EROWS = RS + 7;          // input rows (7 tap rows + 1 zero-weight row)
+constexpr int UR = RS + 7, UC = RS + 8;
+constexpr int NTHR = 160;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
+
+struct TcSmem {
+    uint4 E[EROWS * RS];        // forward A operand: entry (row, x) = 8 bf16 of u(row, x..x+7)
+    uint4 Wf[8 * 48];           // forward B operand [tap row a][filter][tap col b]
+    uint4 Wa[6 * 64];           // adjoint B operand [filter group][tap 8a+b][filter in group]
+    uint4 Psi[2][6 * 128];      // adjoint A operand [buffer][filter group][pixel][filter in group]
+    float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
+    float U[UR * UC];           // fp32 input region
+    uint64_t bar[11];
+    uint32_t tmem_base;
+    int abort_flag;
+    float red[NTHR / 32];
+};
+
+enum { B_FWD = 0, B_REMPTY = 2, B_PSI = 4, B_ADJ = 6, B_ZEMPTY = 8, B_DRAIN = 10 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if the CTA gave up.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
+{
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 31u) == 31u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kTimeoutCycles) {
+                *abort_flag = 1;
+                atomicExch(status, (int)5 /* FOE_ETIMEOUT */);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // K-major, no swizzle: core matrices of 8 rows x 16 B; lbo = next core matrix along K,
+    // sbo = next group of 8 rows; bits 46-47 = descriptor version 1.
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
+{
+    // D FP32 (bit 4), A BF16 (bits 7-9 = 1), B BF16 (bits 10-12 = 1), both K-major,
+    // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Sum of the horizontal partials at (qy, qx) of the response region over the 7 tap rows; rows and
+// columns outside the region are outside the image whenever they are asked for, so they add 0.
+__device__ __forceinline__ float hs_gather(const TcSmem &S, int qy, int qx)
+{
+    if (qx < 0 || qx >= RS) return 0.0f;
+    float g = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        const int r = qy - a + 3;
+        if (r >= 0 && r < RS) g += S.Hs[(a * RS + r) * RS + qx];
+    }
+    return g;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int im = tile_image(A, tile);
+    const ImgDesc &D = A.img[im];
+    const int lt = tile - A.tile_prefix[im];
+    const int oy0 = (lt / D.tiles_x) * TO, ox0 = (lt % D.tiles_x) * TO;
+    const int H = D.H, W = D.W, ld = D.ld;
+    const float *uin = D.u_hi[A.parity];
+
+    // an earlier launch that gave up leaves *status set: then do nothing (CTA-uniform decision)
+    if (tid == 0) S.abort_flag = *(volatile int *)status;
+    __syncthreads();
+    if (S.abort_flag) return;
+    __syncthreads();
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.bar[B_FWD + b], 1);
+            mbar_init(&S.bar[B_REMPTY + b], 128);
+            mbar_init(&S.bar[B_PSI + b], 128);
+            mbar_init(&S.bar[B_ADJ + b], 1);
+            mbar_init(&S.bar[B_ZEMPTY + b], 128);
+        }
+        mbar_init(&S.bar[B_DRAIN], 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+
+    // ---- operands: filter images (prepared on the host as bf16) and the tile ----
+    const uint4 *ops = reinterpret_cast<const uint4 *>(A.tcops);
+    for (int j = tid; j < 8 * 48 + 6 * 64; j += NTHR) {
+        const uint4 v = __ldg(ops + j);
+        if (j < 8 * 48) S.Wf[j] = v;
+        else S.Wa[j - 8 * 48] = v;
+    }
+    float lsum = 0.0f;
+    for (int j = tid; j < UR * UR; j += NTHR) {
+        const int r = j / UR, c = j % UR;
+        const int sy = pad_index(oy0 - 6 + r, H, A.bc), sx = pad_index(ox0 - 6 + c, W, A.bc);
+        const float v = (sy < 0 || sx < 0) ? 0.0f : __ldg(uin + (size_t)sy * ld + sx);
+        S.U[r * UC + c] = v;
+        lsum += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) S.red[warp] = lsum;
+    __syncthreads();
+    float mean = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NTHR / 32; ++w) mean += S.red[w];
+    mean *= 1.0f / (float)(UR * UR);
+    for (int j = tid; j < EROWS * RS; j += NTHR) {
+        const int i = j / RS, x = j % RS;
+        const float *src = &S.U[i * UC + x];
+        uint4 e;
+        e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
+        e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
+        e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
+        e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
+        S.E[j] = e;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+    volatile int *abort_flag = &S.abort_flag;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- MMA issue ----------------
+            constexpr uint32_t IDF = idesc_bf16(128, 48), IDA = idesc_bf16(128, 64);
+            const uint32_t e0 = smem_u32(S.E), wf0 = smem_u32(S.Wf), wa0 = smem_u32(S.Wa);
+            bool ok = true;
+            auto adjoint = [&](int t) {
+                const int b = t & 1, k = t >> 1;
+                if (!mbar_wait(&S.bar[B_PSI + b], k & 1, abort_flag, status)) return false;
+                if (t >= 2 && !mbar_wait(&S.bar[B_ZEMPTY + b], (k - 1) & 1, abort_flag, status)) return false;
+                fence_after();
+                const uint32_t ps = smem_u32(S.Psi[b]);
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+                    mma_bf16(tmem + 128 + 64 * b, sdesc(ps + s * 2 * 2048, 2048, 128), sdesc(wa0 + s * 2 * 1024, 1024, 128),
+                             IDA, s > 0);
+                mma_commit(&S.bar[B_ADJ + b]);
+                return true;
+            };
+            for (int t = 0; t < NMT && ok; ++t) {
+                const int b = t & 1, k = t >> 1;
+                if (t >= 2 && !mbar_wait(&S.bar[B_REMPTY + b], (k - 1) & 1, abort_flag, status)) { ok = false; break; }
+                fence_after();
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_bf16(tmem + 64 * b, sdesc(e0 + (4 * t + 2 * s) * RS * 16, RS * 16, 128),
+                             sdesc(wf0 + s * 2 * 768, 768, 128), IDF, s > 0);
+                mma_commit(&S.bar[B_FWD + b]);
+                if (t >= 1 && !adjoint(t - 1)) ok = false;
+            }
+            if (ok) adjoint(NMT - 1);
+            // all MMAs issued by this thread are complete once the drain barrier flips
+            mma_commit(&S.bar[B_DRAIN]);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&S.bar[B_DRAIN], 0))
+                if (clock64() - t0 > kTimeoutCycles) {
+                    atomicExch(status, 5);
+                    break;
+                }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps: TMEM <-> registers, pointwise work ----------------
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        const int m = 32 * warp + lane;
+        auto col2im = [&](int t) {
+            const int b = t & 1, k = t >> 1;
+            if (!mbar_wait(&S.bar[B_ADJ + b], k & 1, abort_flag, status)) return false;
+            fence_after();
+            float z[64];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + 128 + 64 * b + 16 * c, z + 16 * c);
+            tmem_wait_ld();
+            fence_before();
+            mbar_arrive(&S.bar[B_ZEMPTY + b]);
+            const int rr = 4 * t + warp;
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                float h = z[8 * a + 3];
+#pragma unroll
+                for (int bb = 0; bb < 7; ++bb) {
+                    if (bb == 3) continue;
+                    const int src = lane + 3 - bb;
+                    const float v = __shfl_sync(0xffffffffu, z[8 * a + bb], src & 31);
+                    h += (src >= 0 && src < 32) ? v : 0.0f;
+                }
+                S.Hs[(a * RS + rr) * RS + lane] = h;
+            }
+            return true;
+        };
+        bool ok = true;
+        for (int t = 0; t < NMT; ++t) {
+            const int b = t & 1, k = t >> 1;
+            if (!mbar_wait(&S.bar[B_FWD + b], k & 1, abort_flag, status)) { ok = false; break; }
+            fence_after();
+            float r[48];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tmem_ld16(tmem + lane_base + 64 * b + 16 * c, r + 16 * c);
+            tmem_wait_ld();
+            fence_before();
+            mbar_arrive(&S.bar[B_REMPTY + b]);
+            const int gy = oy0 - 3 + 4 * t + warp, gx = ox0 - 3 + lane;
+            const float msk = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? 1.0f : 0.0f;
+            uint32_t w[24];
+#pragma unroll
+            for (int j = 0; j < 24; ++j) {
+                const float r0 = r[2 * j], r1 = r[2 * j + 1];
+                const float p0 = msk * r0 * rcp_approx(fmaf(r0, r0, 1.0f));
+                const float p1 = msk * r1 * rcp_approx(fmaf(r1, r1, 1.0f));
+                w[j] = pack_bf16x2(p0, p1);
+            }
+            uint4 *dst = &S.Psi[b][m];
+#pragma unroll
+            for (int kc = 0; kc < 6; ++kc) dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+            fence_async_smem();
+            mbar_arrive(&S.bar[B_PSI + b]);
+            if (t >= 1 && !col2im(t - 1)) { ok = false; break; }
+        }
+        if (ok) col2im(NMT - 1);
+    }
+
+    fence_before();
+    __syncthreads();
+
+    // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
+    const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TO > H - 3 || ox0 + TO > W - 3);
+    for (int j = tid; j < TO * TO; j += NTHR) {
+        const int yo = 3 + j / TO, xo = 3 + j % TO;
+        const int gy = oy0 + yo - 3, gx = ox0 + xo - 3;
+        if (gy >= H || gx >= W) continue;
+        float g = hs_gather(S, yo, xo);
+        if (ring) {
+            const int my = gy < 3 ? -1 - gy : (gy >= H - 3 ? 2 * H - 1 - gy : -1000);
+            const int mx = gx < 3 ? -1 - gx : (gx >= W - 3 ? 2 * W - 1 - gx : -1000);
+            if (my != -1000) g += hs_gather(S, my - oy0 + 3, xo);
+            if (mx != -1000) g += hs_gather(S, yo, mx - ox0 + 3);
+            if (my != -1000 && mx != -1000) g += hs_gather(S, my - oy0 + 3, mx - ox0 + 3);
+        }
+        const size_t idx = (size_t)gy * ld + gx;
+        const float uh = S.U[(yo + 3) * UC + xo + 3];
+        if (MODE == kGrad) {
+            D.out[idx] = g + data_grad(uh, D.d[idx], D.model, D.sc.lambda);
+        } else {
+            const float ul = D.u_lo ? D.u_lo[idx] : 0.0f;
+            float nh, nl, nd;
+            ipiano_update(g, uh, ul, D.delta[idx], D.d[idx], D.model, D.sc, nh, nl, nd);
+            D.u_hi[A.parity ^ 1][idx] = nh;
+            if (D.u_lo) D.u_lo[idx] = nl;
+            D.delta[idx] = nd;
+        }
+    }
+
+    if (warp == 4) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace
+
+int tc_tile_h() { return TO; }
+int tc_tile_w() { return TO; }
+size_t tc_smem_bytes() { return sizeof(TcSmem); }
+
+cudaError_t tc_setup()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem))))
+        return e;
+    return cudaFuncSetAttribute(k_foe_tc<kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+}
+
+cudaError_t tc_launch(const LaunchArgs &a, int mode, int *d_status, cudaStream_t s)
+{
+    const int tiles = a.tile_prefix[a.nimg];
+    if (tiles <= 0) return cudaSuccess;
+    if (mode == kStep) k_foe_tc<kStep><<<tiles, NTHR, sizeof(TcSmem), s>>>(a, d_status);
+    else if (mode == kGrad) k_foe_tc<kGrad><<<tiles, NTHR, sizeof(TcSmem), s>>>(a, d_status);
+    else return cudaErrorNotSupported;
+    return cudaGetLastError();
+}
+
 }  // namespace foe
