@@ -121,7 +121,7 @@ def ncu_traffic(kernel_key: str):
     e = t.get(kernel_key)
     if not e or e.get("source_sha") != kernel_source_sha():
         return None
-    return e.get("bytes_per_launch_512x512x10")
+    return e.get("bytes_per_launch")
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) timing
@@ -187,8 +187,14 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--main-only", action="store_true",
+                    help="time the main path only (no FP32 comparison, single-image or end-to-end legs); "
+                         "used for profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.main_only:
+        args.fp32_steps = 0
+        args.no_cpu_baseline = True
 
     if args.impl == "reference":
         return run_reference(args)
@@ -306,6 +312,16 @@ def main():
         fp32 = {"value": world * pix_iters_step * args.fp32_steps / (t32 / 1e3) / 1e6, "unit": "MPix·iter/s",
                 "ms_per_step": t32 / args.fp32_steps,
                 "avg_launch_us": (l32 / 1e3) / max(n32, 1) * 1e6}
+
+    if args.main_only:
+        F.foe_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "MPix·iter/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                              "dtype": dtype, "roofline": roofline, "clocks": clocks, "main_only": True}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
 
     # single-image latency (one 512x512 image, 300 iterations, A2 model at peak 8)
     xs1 = torch.empty((H, ld), dtype=torch.float32, device=dev)
