@@ -135,6 +135,25 @@ FOE_API foe_status foe_prior_lipschitz(const foe_prior *prior, foe_bc bc, double
 FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *opts, void *stream, foe_report *rep);
 
+/* foe_denoise for callers that cannot allocate device memory at the time of the call: code that runs
+ * while a CUDA graph is being captured (cudaMalloc is not permitted under global capture), code whose
+ * device memory is owned entirely by another allocator (a framework's caching allocator or a fixed
+ * arena), and real-time loops that cannot afford cudaMalloc's implicit device synchronisation.  It
+ * computes exactly what foe_denoise computes, but its workspace is a fixed 20 MiB device array inside
+ * the library instead of context memory; it never calls cudaMalloc, cudaFree or any allocating
+ * routine.  The paper has no counterpart of this entry point.
+ *   - Size limit: H * ld <= 1048576 floats (e.g. 1024 x 1024); larger images return FOE_EINVAL with a
+ *     message, before any device work.
+ *   - The array is shared by every call in the process on a device and keeps the last call's contents;
+ *     calls whose work overlaps on the GPU (other streams, other threads) race on it.  Serialise them.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress), with
+ *     that device current; make that first call before any stream capture begins.
+ *   - No report and no profiling: nothing is synchronised.  The context (created earlier, when
+ *     allocation was possible) supplies the filters.
+ * Arguments and the other errors are those of foe_denoise. */
+FOE_API foe_status foe_denoise_static(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
+                                      const foe_solve_opts *opts, void *stream);
+
 /* Denoises n independent images of mixed sizes and iteration budgets in one stream-ordered pass:
  * every iteration advances all images whose budget is not yet spent, in one launch over the tiles
  * of all of them.  opts->iters is ignored (each desc carries its own). */

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/foe.h"
@@ -660,3 +661,93 @@ foe_status foe_inverse(const float *z, float *x, long n, void *stream)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Denoising without any allocation: the workspace of foe_denoise_static lives in a fixed device array
+// of this file instead of memory obtained with cudaMalloc.
+// ------------------------------------------------------------------------------------------------
+
+// Five planes (u_hi[2], u_lo, delta, d) of at most kStaticMaxPlane floats each: 20 MiB, held on every
+// device that loads the library until the process exits.
+static constexpr size_t kStaticMaxPlane = (size_t)1 << 20;
+static __device__ __align__(256) float g_static_ws[5 * kStaticMaxPlane];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+float *g_static_ws_ptr[kStaticMaxDevices] = {};
+std::mutex g_static_ws_mu;
+
+// Device address of g_static_ws on the current device, looked up once per device.  In host code the
+// name g_static_ws is only a host-side stand-in, so kernels must be given this address instead.
+foe_status static_workspace(foe_ctx *c, float **out)
+{
+    int dev = 0;
+    FOE_CUDA(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) {
+        set_err(c, "device ordinal %d is beyond the %d devices foe_denoise_static supports", dev, kStaticMaxDevices);
+        return FOE_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_static_ws_mu);
+    if (!g_static_ws_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+        if (e != cudaSuccess || !p) {
+            set_err(c, "cudaGetSymbolAddress(g_static_ws) failed: %s", cudaGetErrorString(e));
+            return FOE_ECUDA;
+        }
+        g_static_ws_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_static_ws_ptr[dev];
+    return FOE_OK;
+}
+
+}  // namespace
+
+extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
+                                         const foe_solve_opts *o, void *stream)
+{
+    if (!c) return FOE_EINVAL;
+    foe_status st;
+    if ((st = check_opts(c, o)) != FOE_OK) return st;
+    if ((st = check_image(c, y, H, W, ld, "y")) != FOE_OK) return st;
+    if ((st = check_image(c, x, H, W, ld, "x")) != FOE_OK) return st;
+    if ((size_t)H * (size_t)ld > kStaticMaxPlane) {
+        set_err(c, "image of %d x %d with pitch %d needs H * ld = %zu floats per plane; the static workspace "
+                   "holds at most %zu (e.g. 1024 x 1024)", H, W, ld, (size_t)H * (size_t)ld, kStaticMaxPlane);
+        return FOE_EINVAL;
+    }
+    if (o->model == FOE_MODEL_AUTO && !(peak > 0.0f && std::isfinite(peak))) {
+        set_err(c, "peak must be > 0 for FOE_MODEL_AUTO");
+        return FOE_EINVAL;
+    }
+    float *ws = nullptr;
+    if ((st = static_workspace(c, &ws)) != FOE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int model = resolve_model(o->model, peak);
+    const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
+    // every plane that the solve reads is written first by k_init (d, u_hi[0], u_lo, delta) or by the
+    // step that precedes the read (u_hi[1]), so the previous call's contents need no clearing
+    Slot sl = carve(ws, (size_t)H * ld);
+    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, sl.ul, sl.delta, s));
+    args_begin(c, o->bc);
+    ImgDesc d{};
+    d.u_hi[0] = sl.uh0;
+    d.u_hi[1] = sl.uh1;
+    d.u_lo = sl.ul;
+    d.delta = sl.delta;
+    d.d = sl.d;
+    d.H = H;
+    d.W = W;
+    d.ld = ld;
+    d.model = model;
+    d.sc = step_consts(tau, o->gamma, o->lambda);
+    args_add(c, o->prec, d);
+    for (int n = 0; n < o->iters; ++n) {
+        c->args.parity = n & 1;
+        if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
+    }
+    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
+    FOE_CUDA(c, foe::launch_output(uf, sl.ul, H, W, ld, ld, model, x, s));
+    return FOE_OK;
+}

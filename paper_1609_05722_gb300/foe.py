@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
             "foe_ipiano_step": (i, [vp, vp, vp, vp, vp, vp, i, i, i, i, f, f, f, i, i, vp]),
             "foe_anscombe": (i, [vp, vp, C.c_long, vp]),
             "foe_inverse": (i, [vp, vp, C.c_long, vp]),
+            "foe_denoise_static": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp]),
             "foe_profile": (i, [vp, i]),
             "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
             "foe_status_string": (C.c_char_p, [i]),
@@ -193,6 +194,14 @@ def foe_denoise(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts
         return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
                 "status": rep.status}
     return None
+
+
+def foe_denoise_static(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts | None = None,
+                       stream=None) -> None:
+    """foe_denoise with the library's fixed device workspace instead of allocated memory (H * ld <= 2**20)."""
+    o = (opts or SolveOpts()).c()
+    _check(lib().foe_denoise_static(ctx, _ptr(y), _ptr(x), H, W, ld, peak, C.byref(o), _stream(stream)), ctx,
+           "foe_denoise_static")
 
 
 def foe_denoise_batch(ctx, descs: list[dict], opts: SolveOpts | None = None, stream=None) -> None:
