@@ -40,7 +40,9 @@ constexpr int RS = TO + 6;             // response region side = 32 = warp width
 constexpr int NMT = RS / 4;            // M-tiles per CTA
 constexpr int EROWS = RS + 7;          // input rows (7 tap rows + 1 zero-weight row)
 constexpr int UR = RS + 7, UC = RS + 8;
-constexpr int NTHR = 160;
+constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quarter
+constexpr int MMA_WARP = NEPI;         // one thread of this warp issues the MMAs
+constexpr int NTHR = 32 * (NEPI + 1);
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 
@@ -51,6 +53,7 @@ struct TcSmem {
     uint4 Psi[2][6 * 128];      // adjoint A operand [buffer][filter group][pixel][filter in group]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
     float U[UR * UC];           // fp32 input region
+    float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
     uint64_t bar[11];
     uint32_t tmem_base;
     int abort_flag;
@@ -151,6 +154,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
     uint32_t d;
@@ -198,40 +216,59 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     __syncthreads();
     if (S.abort_flag) return;
     __syncthreads();
+
+    // ---- asynchronous staging: group 0 = input region + filter images, group 1 = output-pass operands ----
+    const uint4 *ops = reinterpret_cast<const uint4 *>(A.tcops);
+    for (int j = tid; j < 8 * 48 + 6 * 64; j += NTHR) cp_async16(j < 8 * 48 ? &S.Wf[j] : &S.Wa[j - 8 * 48], ops + j);
+    for (int j = tid; j < UR * UR; j += NTHR) {
+        const int r = j / UR, c = j % UR;
+        const int sy = pad_index(oy0 - 6 + r, H, A.bc), sx = pad_index(ox0 - 6 + c, W, A.bc);
+        if (sy < 0 || sx < 0) S.U[r * UC + c] = 0.0f;
+        else cp_async4(&S.U[r * UC + c], uin + (size_t)sy * ld + sx);
+    }
+    cp_async_commit();
+    if (MODE == kStep) {
+        for (int j = tid; j < TO * TO; j += NTHR) {
+            const int gy = oy0 + j / TO, gx = ox0 + j % TO;
+            if (gy >= H || gx >= W) continue;
+            const size_t idx = (size_t)gy * ld + gx;
+            if (D.u_lo) cp_async4(&S.O[0][j], D.u_lo + idx);
+            else S.O[0][j] = 0.0f;
+            cp_async4(&S.O[1][j], D.delta + idx);
+            cp_async4(&S.O[2][j], D.d + idx);
+        }
+    } else {
+        for (int j = tid; j < TO * TO; j += NTHR) {
+            const int gy = oy0 + j / TO, gx = ox0 + j % TO;
+            if (gy < H && gx < W) cp_async4(&S.O[2][j], D.d + (size_t)gy * ld + gx);
+        }
+    }
+    cp_async_commit();
+
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&S.bar[B_FWD + b], 1);
-            mbar_init(&S.bar[B_REMPTY + b], 128);
-            mbar_init(&S.bar[B_PSI + b], 128);
+            mbar_init(&S.bar[B_REMPTY + b], 32 * NEPI);
+            mbar_init(&S.bar[B_PSI + b], 32 * NEPI);
             mbar_init(&S.bar[B_ADJ + b], 1);
-            mbar_init(&S.bar[B_ZEMPTY + b], 128);
+            mbar_init(&S.bar[B_ZEMPTY + b], 32 * NEPI);
         }
         mbar_init(&S.bar[B_DRAIN], 1);
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 
-    // ---- operands: filter images (prepared on the host as bf16) and the tile ----
-    const uint4 *ops = reinterpret_cast<const uint4 *>(A.tcops);
-    for (int j = tid; j < 8 * 48 + 6 * 64; j += NTHR) {
-        const uint4 v = __ldg(ops + j);
-        if (j < 8 * 48) S.Wf[j] = v;
-        else S.Wa[j - 8 * 48] = v;
-    }
+    // ---- tile mean (BF16 range), then E ----
+    cp_async_wait<1>();
+    __syncthreads();
     float lsum = 0.0f;
-    for (int j = tid; j < UR * UR; j += NTHR) {
-        const int r = j / UR, c = j % UR;
-        const int sy = pad_index(oy0 - 6 + r, H, A.bc), sx = pad_index(ox0 - 6 + c, W, A.bc);
-        const float v = (sy < 0 || sx < 0) ? 0.0f : __ldg(uin + (size_t)sy * ld + sx);
-        S.U[r * UC + c] = v;
-        lsum += v;
-    }
+    for (int j = tid; j < UR * UR; j += NTHR) lsum += S.U[(j / UR) * UC + j % UR];
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0) S.red[warp] = lsum;
     __syncthreads();
@@ -256,7 +293,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     const uint32_t tmem = S.tmem_base;
     volatile int *abort_flag = &S.abort_flag;
 
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         if (lane == 0) {
             // ---------------- MMA issue ----------------
             constexpr uint32_t IDF = idesc_bf16(128, 48), IDA = idesc_bf16(128, 64);
@@ -298,28 +335,34 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps: TMEM <-> registers, pointwise work ----------------
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-        const int m = 32 * warp + lane;
+        // ---------------- epilogue warps ----------------
+        // warp q = warp % 4 reads TMEM lanes 32q..32q+31 (response row 4t+q of M-tile t); the two warps of a
+        // lane quarter split the filters (half = 0: filters 0-23, 1: 24-47) and the tap rows (0: a 0-3, 1: a 4-6).
+        const int q = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const int m = 32 * q + lane;
         auto col2im = [&](int t) {
             const int b = t & 1, k = t >> 1;
             if (!mbar_wait(&S.bar[B_ADJ + b], k & 1, abort_flag, status)) return false;
             fence_after();
-            float z[64];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + 128 + 64 * b + 16 * c, z + 16 * c);
+            float z[32];
+            const uint32_t zc = tmem + lane_base + 128 + 64 * b + 32 * half;
+            tmem_ld16(zc, z);
+            tmem_ld16(zc + 16, z + 16);
             tmem_wait_ld();
             fence_before();
             mbar_arrive(&S.bar[B_ZEMPTY + b]);
-            const int rr = 4 * t + warp;
+            const int rr = 4 * t + q;
 #pragma unroll
-            for (int a = 0; a < 7; ++a) {
-                float h = z[8 * a + 3];
+            for (int aa = 0; aa < 4; ++aa) {
+                const int a = 4 * half + aa;
+                if (a > 6) break;
+                float h = z[8 * aa + 3];
 #pragma unroll
                 for (int bb = 0; bb < 7; ++bb) {
                     if (bb == 3) continue;
                     const int src = lane + 3 - bb;
-                    const float v = __shfl_sync(0xffffffffu, z[8 * a + bb], src & 31);
+                    const float v = __shfl_sync(0xffffffffu, z[8 * aa + bb], src & 31);
                     h += (src >= 0 && src < 32) ? v : 0.0f;
                 }
                 S.Hs[(a * RS + rr) * RS + lane] = h;
@@ -331,25 +374,26 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             const int b = t & 1, k = t >> 1;
             if (!mbar_wait(&S.bar[B_FWD + b], k & 1, abort_flag, status)) { ok = false; break; }
             fence_after();
-            float r[48];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) tmem_ld16(tmem + lane_base + 64 * b + 16 * c, r + 16 * c);
+            float r[24];
+            const uint32_t rc = tmem + lane_base + 64 * b + 24 * half;
+            tmem_ld16(rc, r);
+            tmem_ld16(rc + 16, r + 16);  // columns 16-31 of this half; only 16-23 are used
             tmem_wait_ld();
             fence_before();
             mbar_arrive(&S.bar[B_REMPTY + b]);
-            const int gy = oy0 - 3 + 4 * t + warp, gx = ox0 - 3 + lane;
-            const float msk = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? 1.0f : 0.0f;
-            uint32_t w[24];
+            const int gy = oy0 - 3 + 4 * t + q, gx = ox0 - 3 + lane;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            uint32_t w[12];
 #pragma unroll
-            for (int j = 0; j < 24; ++j) {
+            for (int j = 0; j < 12; ++j) {
                 const float r0 = r[2 * j], r1 = r[2 * j + 1];
-                const float p0 = msk * r0 * rcp_approx(fmaf(r0, r0, 1.0f));
-                const float p1 = msk * r1 * rcp_approx(fmaf(r1, r1, 1.0f));
-                w[j] = pack_bf16x2(p0, p1);
+                const float p0 = r0 * rcp_approx(fmaf(r0, r0, 1.0f));
+                const float p1 = r1 * rcp_approx(fmaf(r1, r1, 1.0f));
+                w[j] = in ? pack_bf16x2(p0, p1) : 0u;
             }
-            uint4 *dst = &S.Psi[b][m];
+            uint4 *dst = &S.Psi[b][(3 * half) * 128 + m];
 #pragma unroll
-            for (int kc = 0; kc < 6; ++kc) dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+            for (int kc = 0; kc < 3; ++kc) dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
             fence_async_smem();
             mbar_arrive(&S.bar[B_PSI + b]);
             if (t >= 1 && !col2im(t - 1)) { ok = false; break; }
@@ -357,6 +401,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (ok) col2im(NMT - 1);
     }
 
+    cp_async_wait<0>();
     fence_before();
     __syncthreads();
 
@@ -377,18 +422,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         const size_t idx = (size_t)gy * ld + gx;
         const float uh = S.U[(yo + 3) * UC + xo + 3];
         if (MODE == kGrad) {
-            D.out[idx] = g + data_grad(uh, D.d[idx], D.model, D.sc.lambda);
+            D.out[idx] = g + data_grad(uh, S.O[2][j], D.model, D.sc.lambda);
         } else {
-            const float ul = D.u_lo ? D.u_lo[idx] : 0.0f;
             float nh, nl, nd;
-            ipiano_update(g, uh, ul, D.delta[idx], D.d[idx], D.model, D.sc, nh, nl, nd);
+            ipiano_update(g, uh, S.O[0][j], S.O[1][j], S.O[2][j], D.model, D.sc, nh, nl, nd);
             D.u_hi[A.parity ^ 1][idx] = nh;
             if (D.u_lo) D.u_lo[idx] = nl;
             D.delta[idx] = nd;
         }
     }
 
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
