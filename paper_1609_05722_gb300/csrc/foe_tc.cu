@@ -45,6 +45,7 @@ constexpr int MMA_WARP = NEPI;         // one thread of this warp issues the MMA
 constexpr int NTHR = 32 * (NEPI + 1);
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
+constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
 struct TcSmem {
     uint4 E[EROWS * RS];        // forward A operand: entry (row, x) = 8 bf16 of u(row, x..x+7)
@@ -54,6 +55,7 @@ struct TcSmem {
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
     float U[UR * UC];           // fp32 input region
     float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
+    int srow[UR], scol[UR];     // source row / column of each input-region row / column (-1: zero)
     uint64_t bar[11];
     uint32_t tmem_base;
     int abort_flag;
@@ -79,10 +81,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0;
 }
@@ -220,9 +222,12 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     // ---- asynchronous staging: group 0 = input region + filter images, group 1 = output-pass operands ----
     const uint4 *ops = reinterpret_cast<const uint4 *>(A.tcops);
     for (int j = tid; j < 8 * 48 + 6 * 64; j += NTHR) cp_async16(j < 8 * 48 ? &S.Wf[j] : &S.Wa[j - 8 * 48], ops + j);
+    if (tid < UR) S.srow[tid] = pad_index(oy0 - 6 + tid, H, A.bc);
+    else if (tid < 2 * UR) S.scol[tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
+    __syncthreads();
     for (int j = tid; j < UR * UR; j += NTHR) {
         const int r = j / UR, c = j % UR;
-        const int sy = pad_index(oy0 - 6 + r, H, A.bc), sx = pad_index(ox0 - 6 + c, W, A.bc);
+        const int sy = S.srow[r], sx = S.scol[c];
         if (sy < 0 || sx < 0) S.U[r * UC + c] = 0.0f;
         else cp_async4(&S.U[r * UC + c], uin + (size_t)sy * ld + sx);
     }
@@ -339,6 +344,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // warp q = warp % 4 reads TMEM lanes 32q..32q+31 (response row 4t+q of M-tile t); the two warps of a
         // lane quarter split the filters (half = 0: filters 0-23, 1: 24-47) and the tap rows (0: a 0-3, 1: a 4-6).
         const int q = warp & 3, half = warp >> 2;
+        // interior tile: the whole response region lies in the image, so no response is masked and no
+        // lane outside 3..28 is ever read (no padding fold)
+        const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + RS - 3 <= H && ox0 + RS - 3 <= W;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int m = 32 * q + lane;
         auto col2im = [&](int t) {
@@ -358,12 +366,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 const int a = 4 * half + aa;
                 if (a > 6) break;
                 float h = z[8 * aa + 3];
+                if (interior) {
 #pragma unroll
-                for (int bb = 0; bb < 7; ++bb) {
-                    if (bb == 3) continue;
-                    const int src = lane + 3 - bb;
-                    const float v = __shfl_sync(0xffffffffu, z[8 * aa + bb], src & 31);
-                    h += (src >= 0 && src < 32) ? v : 0.0f;
+                    for (int bb = 0; bb < 3; ++bb) h += __shfl_down_sync(0xffffffffu, z[8 * aa + bb], 3 - bb);
+#pragma unroll
+                    for (int bb = 4; bb < 7; ++bb) h += __shfl_up_sync(0xffffffffu, z[8 * aa + bb], bb - 3);
+                } else {
+#pragma unroll
+                    for (int bb = 0; bb < 7; ++bb) {
+                        if (bb == 3) continue;
+                        const int src = lane + 3 - bb;
+                        const float v = __shfl_sync(0xffffffffu, z[8 * aa + bb], src & 31);
+                        h += (src >= 0 && src < 32) ? v : 0.0f;
+                    }
                 }
                 S.Hs[(a * RS + rr) * RS + lane] = h;
             }
@@ -382,7 +397,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             fence_before();
             mbar_arrive(&S.bar[B_REMPTY + b]);
             const int gy = oy0 - 3 + 4 * t + q, gx = ox0 - 3 + lane;
-            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const bool in = interior || (gy >= 0 && gy < H && gx >= 0 && gx < W);
             uint32_t w[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
