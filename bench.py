@@ -176,6 +176,105 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving leg
+
+def serving_pool(rank: int):
+    """Page-locked pool of noisy images that requests are cropped from (generating 2000 fresh images would
+    dominate the run): 2048^2 natural-image stand-ins at 4 peaks and one 4096^2 microscopy-like tile."""
+    import torch
+    from paper_1609_05722_gb300 import synth
+    pool = {}
+    for j, peak in enumerate((1.5, 3.0, 8.0, 20.0)):
+        c = synth.clean_image(2048, 2048, 7000 + j + 100 * rank)
+        pool[peak] = torch.from_numpy(synth.poisson_observation(c, peak, 7100 + j + 100 * rank).astype(np.float32)).pin_memory()
+    c = synth.microscopy_tile(4096, 4096, 7200 + rank)
+    pool["micro"] = torch.from_numpy(synth.poisson_observation(c, 1.5, 7201 + rank).astype(np.float32)).pin_memory()
+    return pool
+
+
+def run_serving(F, ctx, pool, n_req: int, rate: float, prec: int, budget: int, per_tick: int, graphs: bool,
+                per_request: bool = False):
+    """Replays a Poisson arrival stream in real time.  Latency = completion time - scheduled arrival time."""
+    import torch
+    from paper_1609_05722_gb300 import synth
+    arrivals = synth.serving_arrivals(n_req, rate, 42)
+    reqs = []
+    rng = np.random.default_rng(4242)
+    for t, spec in arrivals:
+        if spec.microscopy:
+            key, side_h, side_w = "micro", 4096, 4096
+        else:
+            key = min((1.5, 3.0, 8.0, 20.0), key=lambda p: abs(np.log(p / spec.peak)))
+            side_h, side_w = 2048, 2048
+        base = pool[key]
+        H, W = min(spec.H, side_h), min(spec.W, side_w)
+        r0 = int(rng.integers(0, side_h - H + 1))
+        c0 = int(rng.integers(0, side_w - W + 1))
+        ptr = base.data_ptr() + 4 * (r0 * side_w + c0)
+        peak = 1.5 if key == "micro" else key
+        view = base.view(side_h, side_w)[r0:r0 + H, c0:c0 + W]
+        reqs.append((t, H, W, ptr, side_w, peak, 150 if peak < 5 else 100, view))
+    out = torch.empty(4096 * 4096, dtype=torch.float32).pin_memory()
+    lat, pix, pix_it = [], 0, 0
+    t0 = time.perf_counter()
+    if per_request:
+        # plain per-request path: one foe_denoise at a time, host copies in and out
+        stream = torch.cuda.current_stream()
+        for (ta, H, W, ptr, pitch, peak, iters, view) in reqs:
+            now = time.perf_counter() - t0
+            if now < ta:
+                time.sleep(ta - now)
+            ld = (W + 3) // 4 * 4
+            yd = torch.empty((H, ld), dtype=torch.float32, device="cuda")
+            yd[:, :W].copy_(view, non_blocking=True)
+            xd = torch.empty_like(yd)
+            F.foe_denoise(ctx, yd, xd, H, W, ld, peak, F.SolveOpts(model=F.FOE_MODEL_AUTO, prec=prec, iters=iters),
+                          stream=stream)
+            out[:H * W].view(H, W).copy_(xd[:, :W], non_blocking=True)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t0 - ta)
+            pix += H * W
+            pix_it += H * W * iters
+        makespan = time.perf_counter() - t0
+        return {"requests": len(reqs), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mpix_per_s": pix / makespan / 1e6,
+                "mpix_iter_per_s": pix_it / makespan / 1e6, "makespan_s": makespan}
+    srv = F.foe_server_create(ctx, budget, 64, per_tick, graphs, F.SolveOpts(model=F.FOE_MODEL_AUTO, prec=prec))
+    arrival_of, size_of = {}, {}
+    i, done = 0, 0
+    try:
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i][0] <= now:
+                ta, H, W, ptr, pitch, peak, iters, _ = reqs[i]
+                rid = F.foe_server_submit(srv, ptr, out.data_ptr(), H, W, peak, iters, y_pitch=pitch, x_pitch=W,
+                                          ctx=ctx)
+                arrival_of[rid] = ta
+                size_of[rid] = (H * W, iters)
+                i += 1
+            st = F.foe_server_get_stats(srv)
+            if st["queued"] == 0 and st["active"] == 0:
+                if i < len(reqs):
+                    time.sleep(max(0.0, reqs[i][0] - (time.perf_counter() - t0)))
+                continue
+            F.foe_server_tick(srv, ctx)
+            tdone = time.perf_counter() - t0
+            for rid in F.foe_server_poll(srv):
+                lat.append(tdone - arrival_of[rid])
+                pix += size_of[rid][0]
+                pix_it += size_of[rid][0] * size_of[rid][1]
+                done += 1
+        st = F.foe_server_get_stats(srv)
+    finally:
+        F.foe_server_destroy(srv)
+    makespan = time.perf_counter() - t0
+    return {"requests": len(reqs), "rate_hz": rate, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mpix_per_s": pix / makespan / 1e6,
+            "mpix_iter_per_s": pix_it / makespan / 1e6, "makespan_s": makespan, "ticks": st["ticks"],
+            "launches": st["launches"], "hbm_budget_gb": budget / 2**30, "peak_state_gb": st["bytes_peak"] / 2**30,
+            "max_active": 64, "iters_per_tick": per_tick, "graphs": graphs}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -187,6 +286,10 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests in the serving leg (Poisson arrivals, 200/s); 0 skips it")
+    ap.add_argument("--serve-baseline-requests", type=int, default=60,
+                    help="prefix of the same stream run through the plain per-request path")
     ap.add_argument("--main-only", action="store_true",
                     help="time the main path only (no FP32 comparison, single-image or end-to-end legs); "
                          "used for profiler captures")
@@ -366,6 +469,18 @@ def main():
     e2e = {"value": world * pix_iters_step * args.steps / t_e2e / 1e6, "unit": "MPix·iter/s",
            "h2d_bytes_per_step": 10 * H * W * 4, "d2h_bytes_per_step": 10 * H * ld * 4}
 
+    # serving leg: continuous batching under a 40 GB budget vs the plain per-request paths
+    serve = None
+    if args.serve_requests > 0:
+        pool = serving_pool(rank)
+        serve = run_serving(F, ctx, pool, args.serve_requests, 200.0, prec_main, 40 << 30, 10, True)
+        if args.serve_baseline_requests > 0:
+            nb = args.serve_baseline_requests
+            serve["per_request_fp32_prefix"] = run_serving(F, ctx, pool, nb, 200.0, F.FOE_PREC_FP32, 0, 0, False, True)
+            serve["per_request_bf16_prefix"] = run_serving(F, ctx, pool, nb, 200.0, prec_main, 0, 0, False, True)
+            serve["batched_prefix"] = run_serving(F, ctx, pool, nb, 200.0, prec_main, 40 << 30, 10, True)
+        del pool
+
     F.foe_destroy(ctx)
     per_step_launches = 2 * (5 + ITERS + 5)
     if rank == 0:
@@ -375,7 +490,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "single_image_ms": float(np.median(lat)),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

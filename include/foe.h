@@ -184,6 +184,47 @@ FOE_API foe_status foe_ipiano_step(foe_ctx *ctx, const float *u_hi, float *u_lo,
 FOE_API foe_status foe_anscombe(const float *y, float *v, long n, void *stream);
 FOE_API foe_status foe_inverse(const float *z, float *x, long n, void *stream);
 
+/* ---- Continuous-batching server ----
+ * Denoise requests of mixed sizes, peaks and iteration budgets are admitted as slots and device
+ * memory free up, iterated together (one step launch per iteration over the tiles of every admitted
+ * request) and retired when their budget is spent.  Every request's iterate state stays on the device
+ * from admission to completion.  One host thread per server. */
+typedef struct foe_server foe_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory for request state; allocated once at creation (>= 1 MiB) */
+    int max_active;           /* requests iterated together, 1..64 */
+    int iters_per_tick;       /* iterations each admitted request advances per tick, >= 1 */
+    int use_graphs;           /* 1: each tick's step launches are captured and replayed as a CUDA graph */
+    foe_solve_opts opts;      /* model, lambda, gamma, tau, bc, prec, zero_c for every request; iters ignored */
+} foe_server_config;
+
+typedef struct {
+    int queued, active;       /* waiting for admission / admitted and iterating */
+    long long completed, ticks, launches;
+    double pixel_iters;       /* pixel-iterations executed so far */
+    size_t bytes_in_use, bytes_peak, bytes_budget;
+} foe_server_stats;
+
+/* Creates a server on a context: allocates the arena (hbm_budget_bytes) and a private stream. */
+FOE_API foe_status foe_server_create(foe_ctx *ctx, const foe_server_config *cfg, foe_server **out);
+/* Waits for the server's work, frees it.  Requests not yet completed are dropped. */
+FOE_API void foe_server_destroy(foe_server *srv);
+/* Queues one request.  y_host: host counts, H x W with row pitch y_pitch floats; x_host: host buffer
+ * for the result (row pitch x_pitch), written by the tick that completes the request.  Both must stay
+ * valid until then (page-locked memory keeps the copies asynchronous).  Never blocks.  FOE_ENOMEM if the
+ * request's state (5 H x ld FP32 planes, ld = W rounded up to 4) exceeds the whole budget. */
+FOE_API foe_status foe_server_submit(foe_server *srv, const float *y_host, int y_pitch, float *x_host, int x_pitch,
+                                     int H, int W, float peak, int iters, long long *id_out);
+/* One scheduling round: admit queued requests in FIFO order while a slot and arena memory are free
+ * (upload + initialise them), advance every admitted request by up to iters_per_tick iterations, then
+ * finish the requests whose budget is spent (output map, copy to x_host, memory returned).  Returns
+ * after the round's device work is complete; *n_completed (nullable) = requests finished this tick. */
+FOE_API foe_status foe_server_tick(foe_server *srv, int *n_completed);
+/* Ids of completed requests not yet polled (up to max_ids), oldest first. */
+FOE_API foe_status foe_server_poll(foe_server *srv, long long *ids, int max_ids, int *n);
+FOE_API foe_status foe_server_get_stats(const foe_server *srv, foe_server_stats *stats);
+
 /* Step-kernel timing (tracing aid).  foe_profile(ctx, 1) clears the counters and starts recording a
  * CUDA event pair around every iteration loop that foe_denoise / foe_denoise_batch enqueue (on the
  * caller's stream); foe_profile(ctx, 0) stops recording.  foe_profile_read waits for the recorded

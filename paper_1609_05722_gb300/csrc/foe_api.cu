@@ -1,302 +1,7 @@
 // C ABI of the FoE denoiser: argument checks, context and workspace, step size, launch sequencing.
-#include <algorithm>
-#include <cstdint>
-#include <cmath>
-#include <complex>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
 #include <mutex>
-#include <vector>
 
-#include "../../include/foe.h"
-#include "foe_kernels.h"
-
-using foe::ImgDesc;
-using foe::LaunchArgs;
-
-struct foe_ctx {
-    int nf = 0;
-    float kconv[foe::kNF * foe::kKK] = {};  // host copy, convolution orientation, zero padded to 48
-    float alpha[foe::kNF] = {};
-    double symbol_max = 0.0;                // max_w sum_i alpha_i |k_i^(w)|^2
-    float *d_wts = nullptr;                 // device [48][49], correlation orientation
-    float *d_alpha = nullptr;               // device [48]
-    void *d_tcops = nullptr;                // device, bf16 operand images of the tensor-core kernel (12 KB)
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    double *d_partials = nullptr;
-    int partials_cap = 0;
-    double *d_energy = nullptr;
-    int *d_status = nullptr;
-    LaunchArgs args;
-    // step-loop timing (foe_profile)
-    bool prof = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
-    long prof_launches = 0;
-    double prof_pixel_iters = 0.0;
-    char err[512] = {};
-};
-
-namespace {
-
-void set_err(foe_ctx *c, const char *fmt, ...)
-{
-    if (!c) return;
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(c->err, sizeof(c->err), fmt, ap);
-    va_end(ap);
-}
-
-#define FOE_CUDA(ctx, call)                                                                    \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess) {                                                               \
-            set_err(ctx, "%s failed: %s", #call, cudaGetErrorString(e_));                      \
-            return e_ == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA;                   \
-        }                                                                                      \
-    } while (0)
-
-// max over an n x n DTFT grid of sum_i alpha_i |k^_i(w)|^2, FP64, separable evaluation:
-// k^(wy, wx) = sum_a e^{-i wy a} sum_b k(a, b) e^{-i wx b}.  |k^(-w)| = |k^(w)| halves the grid.
-double symbol_max(const float *k, const float *alpha, int nf, int n)
-{
-    using cd = std::complex<double>;
-    std::vector<cd> E((size_t)n * foe::kKS);
-    for (int i = 0; i < n; ++i)
-        for (int a = 0; a < foe::kKS; ++a) {
-            const double ph = -2.0 * M_PI * (double)i * (a - foe::kR) / n;
-            E[(size_t)i * foe::kKS + a] = cd(std::cos(ph), std::sin(ph));
-        }
-    std::vector<cd> R((size_t)nf * foe::kKS * n);
-    for (int f = 0; f < nf; ++f)
-        for (int a = 0; a < foe::kKS; ++a)
-            for (int ix = 0; ix < n; ++ix) {
-                cd s = 0.0;
-                for (int b = 0; b < foe::kKS; ++b)
-                    s += (double)k[f * foe::kKK + a * foe::kKS + b] * E[(size_t)ix * foe::kKS + b];
-                R[((size_t)f * foe::kKS + a) * n + ix] = s;
-            }
-    double best = 0.0;
-    for (int iy = 0; iy <= n / 2; ++iy)
-        for (int ix = 0; ix < n; ++ix) {
-            double s = 0.0;
-            for (int f = 0; f < nf; ++f) {
-                cd v = 0.0;
-                for (int a = 0; a < foe::kKS; ++a) v += E[(size_t)iy * foe::kKS + a] * R[((size_t)f * foe::kKS + a) * n + ix];
-                s += (double)alpha[f] * std::norm(v);
-            }
-            best = std::max(best, s);
-        }
-    return best;
-}
-
-uint16_t f32_to_bf16(float f)
-{
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even (inputs are finite)
-    return (uint16_t)(u >> 16);
-}
-
-// bf16 operand images of the tensor-core kernel, from correlation weights w[48][49] and alpha:
-//   forward B  [tap row a (8)][filter (48)][tap col b (8)] = w_f(a, b)          (0 for a or b = 7)
-//   adjoint B  [filter group (6)][tap 8a+b (64)][filter in group (8)] = 2 alpha_f w_f(a, b)
-std::vector<uint16_t> tc_operands(const float *w, const float *alpha)
-{
-    std::vector<uint16_t> out(8 * 48 * 8 + 6 * 64 * 8, 0);
-    for (int a = 0; a < 8; ++a)
-        for (int f = 0; f < 48; ++f)
-            for (int b = 0; b < 8; ++b)
-                out[(a * 48 + f) * 8 + b] = (a < 7 && b < 7) ? f32_to_bf16(w[f * foe::kKK + a * 7 + b]) : 0;
-    uint16_t *adj = out.data() + 8 * 48 * 8;
-    for (int g = 0; g < 6; ++g)
-        for (int n = 0; n < 64; ++n)
-            for (int e = 0; e < 8; ++e) {
-                const int f = 8 * g + e, a = n / 8, b = n % 8;
-                adj[(g * 64 + n) * 8 + e] = (a < 7 && b < 7) ? f32_to_bf16(2.0f * alpha[f] * w[f * foe::kKK + a * 7 + b]) : 0;
-            }
-    return out;
-}
-
-foe_status check_prior(const foe_prior *p)
-{
-    if (!p || !p->filters || !p->alpha) return FOE_EINVAL;
-    if (p->nf < 1 || p->nf > foe::kNF || p->ksize != foe::kKS) return FOE_EINVAL;
-    for (int i = 0; i < p->nf; ++i)
-        if (!(p->alpha[i] > 0.0f) || !std::isfinite(p->alpha[i])) return FOE_EINVAL;
-    for (int i = 0; i < p->nf * foe::kKK; ++i)
-        if (!std::isfinite(p->filters[i])) return FOE_EINVAL;
-    return FOE_OK;
-}
-
-double kappa(int bc) { return bc == foe::kZero ? 1.0 : 4.0; }
-
-float default_tau(double symbol, int bc, float gamma)
-{
-    const double L = 2.0 * kappa(bc) * symbol;
-    return (float)(0.99 * 2.0 * (1.0 - (double)gamma) / (L + 2e-3));
-}
-
-foe_status check_opts(foe_ctx *c, const foe_solve_opts *o)
-{
-    if (!o) { set_err(c, "opts is NULL"); return FOE_EINVAL; }
-    if (o->model < FOE_MODEL_DIRECT || o->model > FOE_MODEL_AUTO) { set_err(c, "bad model"); return FOE_EINVAL; }
-    if (!(o->lambda > 0.0f) || !std::isfinite(o->lambda)) { set_err(c, "lambda must be > 0"); return FOE_EINVAL; }
-    if (!(o->gamma >= 0.0f && o->gamma < 1.0f)) { set_err(c, "gamma must be in [0, 1)"); return FOE_EINVAL; }
-    if (!(o->tau >= 0.0f) || !std::isfinite(o->tau)) { set_err(c, "tau must be >= 0"); return FOE_EINVAL; }
-    if (o->iters < 0) { set_err(c, "iters must be >= 0"); return FOE_EINVAL; }
-    if (o->step != FOE_STEP_FIXED) { set_err(c, "only FOE_STEP_FIXED is implemented"); return FOE_EUNSUPPORTED; }
-    if (o->bc != FOE_BC_SYMMETRIC && o->bc != FOE_BC_ZERO) { set_err(c, "bad bc"); return FOE_EINVAL; }
-    if (o->prec != FOE_PREC_FP32 && o->prec != FOE_PREC_BF16 && o->prec != FOE_PREC_TF32) {
-        set_err(c, "bad precision");
-        return FOE_EINVAL;
-    }
-    if (o->prec == FOE_PREC_TF32) { set_err(c, "TF32 convolutions are not implemented"); return FOE_EUNSUPPORTED; }
-    if (!(o->zero_c >= 0.0f) || !std::isfinite(o->zero_c)) { set_err(c, "zero_c must be >= 0"); return FOE_EINVAL; }
-    return FOE_OK;
-}
-
-foe_status check_image(foe_ctx *c, const void *p, int H, int W, int ld, const char *what)
-{
-    if (!p) { set_err(c, "%s is NULL", what); return FOE_EINVAL; }
-    if (H < 7 || W < 7) { set_err(c, "%s: H and W must be >= 7 (got %d x %d)", what, H, W); return FOE_EINVAL; }
-    if (ld < W || ld % 4 != 0) { set_err(c, "%s: ld must be >= W and a multiple of 4 (got %d)", what, ld); return FOE_EINVAL; }
-    if ((reinterpret_cast<uintptr_t>(p) & 15) != 0) { set_err(c, "%s must be 16-byte aligned", what); return FOE_EINVAL; }
-    return FOE_OK;
-}
-
-int resolve_model(int model, float peak) { return model == FOE_MODEL_AUTO ? (peak >= 5.0f ? foe::kAnsL2 : foe::kAnsIdiv) : model; }
-
-foe::StepConsts step_consts(float tau, float gamma, float lambda)
-{
-    foe::StepConsts s;
-    s.tau = tau;
-    s.gamma = gamma;
-    s.lambda = lambda;
-    const double c = (double)tau * (double)lambda;
-    auto split = [](double v, float &hi, float &lo) {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
-    };
-    split(c, s.c_hi, s.c_lo);
-    split(1.0 / (1.0 + c), s.a1_hi, s.a1_lo);
-    split(c / (1.0 + c), s.a2_hi, s.a2_lo);
-    return s;
-}
-
-void tile_dims(int prec, int &th, int &tw)
-{
-    if (prec == FOE_PREC_BF16) {
-        th = foe::tc_tile_h();
-        tw = foe::tc_tile_w();
-    } else {
-        th = tw = foe::f32_tile();
-    }
-}
-
-void args_begin(foe_ctx *c, int bc)
-{
-    LaunchArgs &A = c->args;
-    A.nimg = 0;
-    A.parity = 0;
-    A.bc = bc;
-    A.nchunks = (c->nf + 7) / 8;
-    A.wts = c->d_wts;
-    A.alpha = c->d_alpha;
-    A.partials = c->d_partials;
-    A.tcops = c->d_tcops;
-    A.tile_prefix[0] = 0;
-}
-
-void args_add(foe_ctx *c, int prec, const ImgDesc &d)
-{
-    LaunchArgs &A = c->args;
-    int th, tw;
-    tile_dims(prec, th, tw);
-    ImgDesc e = d;
-    e.tiles_x = (d.W + tw - 1) / tw;
-    const int tiles = e.tiles_x * ((d.H + th - 1) / th);
-    A.img[A.nimg] = e;
-    A.tile_prefix[A.nimg + 1] = A.tile_prefix[A.nimg] + tiles;
-    A.nimg++;
-}
-
-foe_status launch(foe_ctx *c, int prec, int mode, cudaStream_t s)
-{
-    cudaError_t e = prec == FOE_PREC_BF16 ? foe::tc_launch(c->args, mode, c->d_status, s) : foe::f32_launch(c->args, mode, s);
-    if (e != cudaSuccess) {
-        set_err(c, "kernel launch failed: %s", cudaGetErrorString(e));
-        return e == cudaErrorNotSupported ? FOE_EUNSUPPORTED : FOE_ECUDA;
-    }
-    return FOE_OK;
-}
-
-foe_status ensure_ws(foe_ctx *c, size_t bytes)
-{
-    if (bytes <= c->ws_bytes) return FOE_OK;
-    if (c->ws) FOE_CUDA(c, cudaFree(c->ws));
-    c->ws = nullptr;
-    c->ws_bytes = 0;
-    FOE_CUDA(c, cudaMalloc(&c->ws, bytes));
-    c->ws_bytes = bytes;
-    return FOE_OK;
-}
-
-foe_status ensure_partials(foe_ctx *c, int n)
-{
-    if (n <= c->partials_cap) return FOE_OK;
-    if (c->d_partials) FOE_CUDA(c, cudaFree(c->d_partials));
-    c->d_partials = nullptr;
-    c->partials_cap = 0;
-    FOE_CUDA(c, cudaMalloc(&c->d_partials, sizeof(double) * (size_t)n));
-    c->partials_cap = n;
-    return FOE_OK;
-}
-
-foe_status prof_begin(foe_ctx *c, cudaStream_t s, cudaEvent_t *ev)
-{
-    ev[0] = ev[1] = nullptr;
-    if (!c->prof) return FOE_OK;
-    FOE_CUDA(c, cudaEventCreate(&ev[0]));
-    FOE_CUDA(c, cudaEventCreate(&ev[1]));
-    FOE_CUDA(c, cudaEventRecord(ev[0], s));
-    return FOE_OK;
-}
-
-foe_status prof_end(foe_ctx *c, cudaStream_t s, cudaEvent_t *ev, long launches, double pixel_iters)
-{
-    if (!ev[0]) return FOE_OK;
-    FOE_CUDA(c, cudaEventRecord(ev[1], s));
-    c->prof_events.emplace_back(ev[0], ev[1]);
-    c->prof_launches += launches;
-    c->prof_pixel_iters += pixel_iters;
-    return FOE_OK;
-}
-
-void prof_clear(foe_ctx *c)
-{
-    for (auto &p : c->prof_events) {
-        cudaEventDestroy(p.first);
-        cudaEventDestroy(p.second);
-    }
-    c->prof_events.clear();
-    c->prof_launches = 0;
-    c->prof_pixel_iters = 0.0;
-}
-
-// Per-image workspace: u_hi[2], u_lo, delta, d, each H x ld floats.
-struct Slot {
-    float *uh0, *uh1, *ul, *delta, *d;
-};
-
-Slot carve(float *base, size_t plane)
-{
-    return Slot{base, base + plane, base + 2 * plane, base + 3 * plane, base + 4 * plane};
-}
-
-}  // namespace
+#include "foe_internal.h"
 
 extern "C" {
 

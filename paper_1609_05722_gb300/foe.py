@@ -45,6 +45,17 @@ class foe_image_desc(C.Structure):
                 ("peak", C.c_float), ("iters", C.c_int)]
 
 
+class foe_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("iters_per_tick", C.c_int),
+                ("use_graphs", C.c_int), ("opts", foe_solve_opts)]
+
+
+class foe_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("completed", C.c_longlong), ("ticks", C.c_longlong),
+                ("launches", C.c_longlong), ("pixel_iters", C.c_double), ("bytes_in_use", C.c_size_t),
+                ("bytes_peak", C.c_size_t), ("bytes_budget", C.c_size_t)]
+
+
 class FoeError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -75,6 +86,12 @@ def lib() -> C.CDLL:
             "foe_anscombe": (i, [vp, vp, C.c_long, vp]),
             "foe_inverse": (i, [vp, vp, C.c_long, vp]),
             "foe_denoise_static": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp]),
+            "foe_server_create": (i, [vp, C.POINTER(foe_server_config), C.POINTER(vp)]),
+            "foe_server_destroy": (None, [vp]),
+            "foe_server_submit": (i, [vp, vp, i, vp, i, i, i, f, i, C.POINTER(C.c_longlong)]),
+            "foe_server_tick": (i, [vp, C.POINTER(i)]),
+            "foe_server_poll": (i, [vp, C.POINTER(C.c_longlong), i, C.POINTER(i)]),
+            "foe_server_get_stats": (i, [vp, C.POINTER(foe_server_stats)]),
             "foe_profile": (i, [vp, i]),
             "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
             "foe_status_string": (C.c_char_p, [i]),
@@ -245,3 +262,52 @@ def foe_profile_read(ctx) -> tuple[float, int, float]:
     ms, n, px = C.c_double(), C.c_long(), C.c_double()
     _check(lib().foe_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(px)), ctx, "foe_profile_read")
     return ms.value, n.value, px.value
+
+
+# ---- continuous-batching server ----
+def foe_server_create(ctx, hbm_budget_bytes: int, max_active: int = 64, iters_per_tick: int = 10,
+                      use_graphs: bool = True, opts: SolveOpts | None = None):
+    cfg = foe_server_config(hbm_budget_bytes, max_active, iters_per_tick, 1 if use_graphs else 0,
+                            (opts or SolveOpts()).c())
+    h = C.c_void_p()
+    _check(lib().foe_server_create(ctx, C.byref(cfg), C.byref(h)), ctx, "foe_server_create")
+    return h.value
+
+
+def foe_server_destroy(srv) -> None:
+    if srv:
+        lib().foe_server_destroy(srv)
+
+
+def foe_server_submit(srv, y_host, x_host, H: int, W: int, peak: float, iters: int, y_pitch: int | None = None,
+                      x_pitch: int | None = None, ctx=None) -> int:
+    """y_host / x_host: host buffers (numpy arrays or torch CPU tensors, ideally page-locked)."""
+    def addr(a):
+        if isinstance(a, int):
+            return a
+        if hasattr(a, "data_ptr"):
+            return int(a.data_ptr())
+        return int(a.ctypes.data)
+    rid = C.c_longlong()
+    _check(lib().foe_server_submit(srv, addr(y_host), y_pitch or W, addr(x_host), x_pitch or W, H, W, peak, iters,
+                                   C.byref(rid)), ctx, "foe_server_submit")
+    return rid.value
+
+
+def foe_server_tick(srv, ctx=None) -> int:
+    n = C.c_int()
+    _check(lib().foe_server_tick(srv, C.byref(n)), ctx, "foe_server_tick")
+    return n.value
+
+
+def foe_server_poll(srv, max_ids: int = 4096) -> list[int]:
+    ids = (C.c_longlong * max_ids)()
+    n = C.c_int()
+    _check(lib().foe_server_poll(srv, ids, max_ids, C.byref(n)), what="foe_server_poll")
+    return list(ids[:n.value])
+
+
+def foe_server_get_stats(srv) -> dict:
+    s = foe_server_stats()
+    _check(lib().foe_server_get_stats(srv, C.byref(s)), what="foe_server_get_stats")
+    return {k: getattr(s, k) for k, _ in foe_server_stats._fields_}
