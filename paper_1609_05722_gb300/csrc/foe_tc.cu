@@ -44,6 +44,9 @@ constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quar
 constexpr int MMA_WARP = NEPI;         // one thread of this warp issues the MMAs
 constexpr int NTHR = 32 * (NEPI + 1);
 constexpr uint32_t TMEM_COLS = 256;
+constexpr int NSTAGE = 4;              // TMEM stages of 64 columns: R (48 columns), then Z over it
+constexpr int NPSI = 3;                // Psi buffers in shared memory
+constexpr int LAG = 2;                 // the adjoint of M-tile g is issued, and its col2im done, 2 M-tiles later
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
@@ -51,18 +54,18 @@ struct TcSmem {
     uint4 E[EROWS * RS];        // forward A operand: entry (row, x) = 8 bf16 of u(row, x..x+7)
     uint4 Wf[8 * 48];           // forward B operand [tap row a][filter][tap col b]
     uint4 Wa[6 * 64];           // adjoint B operand [filter group][tap 8a+b][filter in group]
-    uint4 Psi[2][6 * 128];      // adjoint A operand [buffer][filter group][pixel][filter in group]
+    uint4 Psi[NPSI][6 * 128];   // adjoint A operand [buffer][filter group][pixel][filter in group]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
     float U[UR * UC];           // fp32 input region
     float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
     int srow[UR], scol[UR];     // source row / column of each input-region row / column (-1: zero)
-    uint64_t bar[11];
+    uint64_t bar[4 * NSTAGE + 1];
     uint32_t tmem_base;
     int abort_flag;
     float red[NTHR / 32];
 };
 
-enum { B_FWD = 0, B_REMPTY = 2, B_PSI = 4, B_ADJ = 6, B_ZEMPTY = 8, B_DRAIN = 10 };
+constexpr int B_FWD = 0, B_PSI = NSTAGE, B_ADJ = 2 * NSTAGE, B_ZEMPTY = 3 * NSTAGE, B_DRAIN = 4 * NSTAGE;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -251,9 +254,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     cp_async_commit();
 
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NSTAGE; ++b) {
             mbar_init(&S.bar[B_FWD + b], 1);
-            mbar_init(&S.bar[B_REMPTY + b], 32 * NEPI);
             mbar_init(&S.bar[B_PSI + b], 32 * NEPI);
             mbar_init(&S.bar[B_ADJ + b], 1);
             mbar_init(&S.bar[B_ZEMPTY + b], 32 * NEPI);
@@ -304,31 +306,33 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             constexpr uint32_t IDF = idesc_bf16(128, 48), IDA = idesc_bf16(128, 64);
             const uint32_t e0 = smem_u32(S.E), wf0 = smem_u32(S.Wf), wa0 = smem_u32(S.Wa);
             bool ok = true;
+            // stage s = t % NSTAGE holds R(t) (columns 64 s .. 64 s + 47) until the epilogue has read it, then
+            // the adjoint writes Z(t) over it (64 columns); the stage is free again once Z(t) has been read.
             auto adjoint = [&](int t) {
-                const int b = t & 1, k = t >> 1;
-                if (!mbar_wait(&S.bar[B_PSI + b], k & 1, abort_flag, status)) return false;
-                if (t >= 2 && !mbar_wait(&S.bar[B_ZEMPTY + b], (k - 1) & 1, abort_flag, status)) return false;
+                const int s = t % NSTAGE, k = t / NSTAGE;
+                if (!mbar_wait(&S.bar[B_PSI + s], k & 1, abort_flag, status)) return false;
                 fence_after();
-                const uint32_t ps = smem_u32(S.Psi[b]);
+                const uint32_t ps = smem_u32(S.Psi[t % NPSI]);
 #pragma unroll
-                for (int s = 0; s < 3; ++s)
-                    mma_bf16(tmem + 128 + 64 * b, sdesc(ps + s * 2 * 2048, 2048, 128), sdesc(wa0 + s * 2 * 1024, 1024, 128),
-                             IDA, s > 0);
-                mma_commit(&S.bar[B_ADJ + b]);
+                for (int kk = 0; kk < 3; ++kk)
+                    mma_bf16(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128), sdesc(wa0 + kk * 2 * 1024, 1024, 128),
+                             IDA, kk > 0);
+                mma_commit(&S.bar[B_ADJ + s]);
                 return true;
             };
             for (int t = 0; t < NMT && ok; ++t) {
-                const int b = t & 1, k = t >> 1;
-                if (t >= 2 && !mbar_wait(&S.bar[B_REMPTY + b], (k - 1) & 1, abort_flag, status)) { ok = false; break; }
+                const int s = t % NSTAGE, k = t / NSTAGE;
+                if (t >= NSTAGE && !mbar_wait(&S.bar[B_ZEMPTY + s], (k - 1) & 1, abort_flag, status)) { ok = false; break; }
                 fence_after();
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    mma_bf16(tmem + 64 * b, sdesc(e0 + (4 * t + 2 * s) * RS * 16, RS * 16, 128),
-                             sdesc(wf0 + s * 2 * 768, 768, 128), IDF, s > 0);
-                mma_commit(&S.bar[B_FWD + b]);
-                if (t >= 1 && !adjoint(t - 1)) ok = false;
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_bf16(tmem + 64 * s, sdesc(e0 + (4 * t + 2 * kk) * RS * 16, RS * 16, 128),
+                             sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
+                mma_commit(&S.bar[B_FWD + s]);
+                if (t >= LAG && !adjoint(t - LAG)) ok = false;
             }
-            if (ok) adjoint(NMT - 1);
+            for (int t = NMT - LAG; ok && t < NMT; ++t)
+                if (!adjoint(t)) ok = false;
             // all MMAs issued by this thread are complete once the drain barrier flips
             mma_commit(&S.bar[B_DRAIN]);
             const long long t0 = clock64();
@@ -350,11 +354,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int m = 32 * q + lane;
         auto col2im = [&](int t) {
-            const int b = t & 1, k = t >> 1;
+            const int b = t % NSTAGE, k = t / NSTAGE;
             if (!mbar_wait(&S.bar[B_ADJ + b], k & 1, abort_flag, status)) return false;
             fence_after();
             float z[32];
-            const uint32_t zc = tmem + lane_base + 128 + 64 * b + 32 * half;
+            const uint32_t zc = tmem + lane_base + 64 * b + 32 * half;
             tmem_ld16(zc, z);
             tmem_ld16(zc + 16, z + 16);
             tmem_wait_ld();
@@ -386,16 +390,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         };
         bool ok = true;
         for (int t = 0; t < NMT; ++t) {
-            const int b = t & 1, k = t >> 1;
+            const int b = t % NSTAGE, k = t / NSTAGE;
             if (!mbar_wait(&S.bar[B_FWD + b], k & 1, abort_flag, status)) { ok = false; break; }
             fence_after();
-            float r[24];
+            float r[32];
             const uint32_t rc = tmem + lane_base + 64 * b + 24 * half;
             tmem_ld16(rc, r);
             tmem_ld16(rc + 16, r + 16);  // columns 16-31 of this half; only 16-23 are used
             tmem_wait_ld();
             fence_before();
-            mbar_arrive(&S.bar[B_REMPTY + b]);
             const int gy = oy0 - 3 + 4 * t + q, gx = ox0 - 3 + lane;
             const bool in = interior || (gy >= 0 && gy < H && gx >= 0 && gx < W);
             uint32_t w[12];
@@ -406,14 +409,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 const float p1 = r1 * rcp_approx(fmaf(r1, r1, 1.0f));
                 w[j] = in ? pack_bf16x2(p0, p1) : 0u;
             }
-            uint4 *dst = &S.Psi[b][(3 * half) * 128 + m];
+            uint4 *dst = &S.Psi[t % NPSI][(3 * half) * 128 + m];
 #pragma unroll
             for (int kc = 0; kc < 3; ++kc) dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
             fence_async_smem();
-            mbar_arrive(&S.bar[B_PSI + b]);
-            if (t >= 1 && !col2im(t - 1)) { ok = false; break; }
+            mbar_arrive(&S.bar[B_PSI + b]);  // R(t) has been read and Psi(t) written: the adjoint may overwrite the stage
+            if (t >= LAG && !col2im(t - LAG)) { ok = false; break; }
         }
-        if (ok) col2im(NMT - 1);
+        for (int t = NMT - LAG; ok && t < NMT; ++t)
+            if (!col2im(t)) ok = false;
     }
 
     cp_async_wait<0>();
