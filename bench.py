@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the leg with 64 uneven images in one CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving leg (Poisson arrivals, 200/s); 0 skips it")
     ap.add_argument("--serve-baseline-requests", type=int, default=60,
@@ -469,6 +471,41 @@ def main():
     e2e = {"value": world * pix_iters_step * args.steps / t_e2e / 1e6, "unit": "MPix·iter/s",
            "h2d_bytes_per_step": 10 * H * W * 4, "d2h_bytes_per_step": 10 * H * ld * 4}
 
+    # batched uneven instances in one graph: 64 images, sides {128..1024}, peaks log-U[1, 30], 100-300 iters
+    batched = None
+    if args.batched:
+        specs = synth.batched_uneven_specs(64, seed=3 + 100 * rank)
+        bys, bxs, bdescs = [], [], []
+        for sp in specs:
+            _, yb = synth.make_problem(sp)
+            ldb = (sp.W + 3) // 4 * 4
+            yd = torch.zeros((sp.H, ldb), dtype=torch.float32, device=dev)
+            yd[:, :sp.W] = torch.from_numpy(yb.astype(np.float32)).to(dev)
+            bys.append(yd)
+            bxs.append(torch.zeros_like(yd))
+            bdescs.append({"y": yd, "x": bxs[-1], "H": sp.H, "W": sp.W, "ld": ldb, "peak": sp.peak, "iters": sp.iters})
+        gstream = torch.cuda.Stream(device=dev)
+        bopts = F.SolveOpts(model=F.FOE_MODEL_AUTO, prec=prec_main, use_graph=True)
+        with torch.cuda.stream(gstream):
+            for _ in range(2):
+                F.foe_denoise_batch(ctx, bdescs, bopts, stream=gstream)
+            gstream.synchronize()
+            times = []
+            for _ in range(3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(gstream)
+                F.foe_denoise_batch(ctx, bdescs, bopts, stream=gstream)
+                e1.record(gstream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        bpix = sum(sp.H * sp.W * sp.iters for sp in specs)
+        batched = {"images": len(specs), "pixel_iters": bpix, "ms": float(np.median(times)),
+                   "value": bpix / (float(np.median(times)) / 1e3) / 1e6, "unit": "MPix·iter/s",
+                   "graph": True, "sides": "H, W independently from {128,256,384,512,768,1024}",
+                   "iters": "U{100..300} per image", "peaks": "log-U[1, 30]"}
+        del bys, bxs, bdescs
+
     # serving leg: continuous batching under a 40 GB budget vs the plain per-request paths
     serve = None
     if args.serve_requests > 0:
@@ -490,7 +527,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "single_image_ms": float(np.median(lat)),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -86,6 +86,11 @@ typedef struct {
     foe_bc bc;
     foe_precision prec;
     float zero_c;         /* direct model: zero counts are replaced by zero_c (Sec. 3.1.1), >= 0 */
+    int use_graph;        /* foe_denoise_batch: 1 = capture the whole batch solve (initialisation, every
+                             iteration launch, output maps) as one CUDA graph and replay it; needs a
+                             non-default stream (on the legacy default stream the launches are issued
+                             directly).  The instantiated graph is cached in the context and updated in
+                             place when the next batch has the same launch structure. */
 } foe_solve_opts;
 
 typedef struct {
@@ -105,7 +110,7 @@ typedef struct {
 } foe_image_desc;
 
 /* Fills *opts with the defaults: AUTO model, lambda 1, gamma 0.8, tau 0 (auto), 300 iterations,
- * fixed steps, symmetric padding, BF16 convolutions, zero_c 0. */
+ * fixed steps, symmetric padding, BF16 convolutions, zero_c 0, no graph capture. */
 FOE_API foe_status foe_default_opts(foe_solve_opts *opts);
 
 /* Creates a context for one prior: validates it, copies the filters to the device and precomputes
@@ -167,6 +172,23 @@ FOE_API foe_status foe_denoise_batch(foe_ctx *ctx, const foe_image_desc *descs, 
 FOE_API foe_status foe_energy_grad(foe_ctx *ctx, const float *u, const float *data, int H, int W, int ld, foe_model model,
                            float lambda, foe_bc bc, foe_precision prec, double *energy_host, float *grad,
                            void *stream);
+
+/* One evaluation of the prior-training objective (Sec. 2.5, Eq. learningmodel) with the loss of Sec. 3.2,
+ *     L = sum_s 1/2 ||I_C(u_s^T) - g_s||^2,
+ * where u_s^T is T = opts->iters unrolled iPiano steps of the Anscombe quadratic model (Eq. overallModel)
+ * from u^0 = u^{-1} = v_s, and of its gradient with respect to the filters and the log-weights
+ * a_i (alpha_i = e^{a_i}), by reverse-mode differentiation of the unrolled iteration with a hand-written
+ * backward kernel (Hessian-vector products of the prior, Sec. 2.5.2).  Iterates are checkpointed every
+ * ckpt_every steps (0: about sqrt(T)) and recomputed segment by segment in the reverse sweep.
+ *   clean, noisy  device, B images of H x W, row pitch ld, image stride H * ld floats (g_s and y_s)
+ *   opts          model must be FOE_MODEL_ANS_L2, prec FOE_PREC_FP32; lambda, gamma, tau (0: default), bc
+ *   loss_host     host, nullable: L (synchronises the stream)
+ *   dfilters      device, [nf][49], dL/dk_i(a, b) in the filters' convolution orientation
+ *   dlogalpha     device, [nf], dL/da_i
+ * The step size tau is held fixed (it is not differentiated). */
+FOE_API foe_status foe_train_step(foe_ctx *ctx, const float *clean, const float *noisy, int B, int H, int W, int ld,
+                                  const foe_solve_opts *opts, int ckpt_every, double *loss_host, float *dfilters,
+                                  float *dlogalpha, void *stream);
 
 /* One iPiano step (Eq. iPianoupdate) on a state given explicitly, for callers that drive the loop:
  *   u_hi, u_lo   device, the iterate u^n = u_hi + u_lo (u_lo may be NULL = zeros; written if not NULL)

@@ -3,6 +3,65 @@
 
 #include "foe_internal.h"
 
+// Enqueues a whole batch solve on s: initialisation, the iteration launches, the output maps.
+static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, const foe_solve_opts *o,
+                                cudaStream_t s, const std::vector<int> &order, int max_iters, bool profile)
+{
+    foe_status st;
+    std::vector<Slot> slots(n);
+    std::vector<int> models(n);
+    float *base = (float *)c->ws;
+    args_begin(c, o->bc);
+    for (int j = 0; j < n; ++j) {
+        const foe_image_desc &d = descs[order[j]];
+        const size_t plane = (size_t)d.H * d.ld;
+        slots[j] = carve(base, plane);
+        base += 5 * plane;
+        models[j] = resolve_model(o->model, d.peak);
+        FOE_CUDA(c, foe::launch_init(d.y, d.H, d.W, d.ld, d.ld, models[j], o->zero_c, slots[j].d, slots[j].uh0,
+                                     slots[j].ul, slots[j].delta, s));
+        const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
+        ImgDesc e{};
+        e.u_hi[0] = slots[j].uh0;
+        e.u_hi[1] = slots[j].uh1;
+        e.u_lo = slots[j].ul;
+        e.delta = slots[j].delta;
+        e.d = slots[j].d;
+        e.H = d.H;
+        e.W = d.W;
+        e.ld = d.ld;
+        e.model = models[j];
+        e.sc = step_consts(tau, o->gamma, o->lambda);
+        args_add(c, o->prec, e);
+    }
+    const int nall = c->args.nimg;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (profile && (st = prof_begin(c, s, ev)) != FOE_OK) return st;
+    double pix = 0.0;
+    for (int it = 0; it < max_iters; ++it) {
+        int active = 0;
+        while (active < nall && descs[order[active]].iters > it) {
+            pix += (double)descs[order[active]].H * descs[order[active]].W;
+            ++active;
+        }
+        c->args.nimg = active;
+        c->args.parity = it & 1;
+        if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) {
+            c->args.nimg = nall;
+            return st;
+        }
+    }
+    c->args.nimg = nall;
+    if (profile && (st = prof_end(c, s, ev, max_iters, pix)) != FOE_OK) return st;
+    for (int j = 0; j < n; ++j) {
+        const foe_image_desc &d = descs[order[j]];
+        const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0;
+        FOE_CUDA(c, foe::launch_output(uf, slots[j].ul, d.H, d.W, d.ld, d.ld, models[j], d.x, s));
+    }
+    return FOE_OK;
+}
+
+
 extern "C" {
 
 const char *foe_status_string(foe_status s)
@@ -35,6 +94,7 @@ foe_status foe_default_opts(foe_solve_opts *o)
     o->bc = FOE_BC_SYMMETRIC;
     o->prec = FOE_PREC_BF16;
     o->zero_c = 0.0f;
+    o->use_graph = 0;
     return FOE_OK;
 }
 
@@ -74,7 +134,7 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) ||
         (e = cudaMemcpy(c->d_wts, w, sizeof(w), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(c->d_status, 0, sizeof(int))) || (e = foe::f32_setup()) || (e = foe::tc_setup()))
+        (e = cudaMemset(c->d_status, 0, sizeof(int))) || (e = foe::f32_setup()) || (e = foe::tc_setup()) || (e = foe::bwd_setup()))
         return fail(e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA);
     (void)st;
     if (ensure_partials(c, 1024) != FOE_OK) return fail(FOE_ENOMEM);
@@ -93,6 +153,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
     cudaFree(c->ws);
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     delete c;
 }
 
@@ -192,57 +253,44 @@ foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, con
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return descs[a].iters > descs[b].iters; });
     if ((st = ensure_ws(c, total * sizeof(float))) != FOE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<Slot> slots(n);
-    std::vector<int> models(n);
-    float *base = (float *)c->ws;
-    args_begin(c, o->bc);
-    for (int j = 0; j < n; ++j) {
-        const foe_image_desc &d = descs[order[j]];
-        const size_t plane = (size_t)d.H * d.ld;
-        slots[j] = carve(base, plane);
-        base += 5 * plane;
-        models[j] = resolve_model(o->model, d.peak);
-        FOE_CUDA(c, foe::launch_init(d.y, d.H, d.W, d.ld, d.ld, models[j], o->zero_c, slots[j].d, slots[j].uh0,
-                                     slots[j].ul, slots[j].delta, s));
-        const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
-        ImgDesc e{};
-        e.u_hi[0] = slots[j].uh0;
-        e.u_hi[1] = slots[j].uh1;
-        e.u_lo = slots[j].ul;
-        e.delta = slots[j].delta;
-        e.d = slots[j].d;
-        e.H = d.H;
-        e.W = d.W;
-        e.ld = d.ld;
-        e.model = models[j];
-        e.sc = step_consts(tau, o->gamma, o->lambda);
-        args_add(c, o->prec, e);
-    }
-    const int nall = c->args.nimg;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FOE_CUDA(c, cudaStreamIsCapturing(s, &cap));
+    const bool graph = o->use_graph && s != nullptr && cap == cudaStreamCaptureStatusNone;
+    if (!graph) return enqueue_batch(c, descs, n, o, s, order, max_iters, !cap);
+    // capture the whole solve, then replay it (updating the cached executable graph when possible)
     cudaEvent_t ev[2];
     if ((st = prof_begin(c, s, ev)) != FOE_OK) return st;
+    FOE_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_batch(c, descs, n, o, s, order, max_iters, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (st != FOE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    FOE_CUDA(c, ec);
+    bool updated = false;
+    if (c->batch_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(c->batch_exec, g, &info) == cudaSuccess;
+        if (!updated) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(c->batch_exec);
+            c->batch_exec = nullptr;
+        }
+    }
+    if (!updated) {
+        const cudaError_t ei = cudaGraphInstantiate(&c->batch_exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            FOE_CUDA(c, ei);
+        }
+    }
+    cudaGraphDestroy(g);
+    FOE_CUDA(c, cudaGraphLaunch(c->batch_exec, s));
     double pix = 0.0;
-    for (int it = 0; it < max_iters; ++it) {
-        int active = 0;
-        while (active < nall && descs[order[active]].iters > it) {
-            pix += (double)descs[order[active]].H * descs[order[active]].W;
-            ++active;
-        }
-        c->args.nimg = active;
-        c->args.parity = it & 1;
-        if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) {
-            c->args.nimg = nall;
-            return st;
-        }
-    }
-    c->args.nimg = nall;
-    if ((st = prof_end(c, s, ev, max_iters, pix)) != FOE_OK) return st;
-    for (int j = 0; j < n; ++j) {
-        const foe_image_desc &d = descs[order[j]];
-        const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0;
-        FOE_CUDA(c, foe::launch_output(uf, slots[j].ul, d.H, d.W, d.ld, d.ld, models[j], d.x, s));
-    }
-    return FOE_OK;
+    for (int j = 0; j < n; ++j) pix += (double)descs[j].H * descs[j].W * descs[j].iters;
+    return prof_end(c, s, ev, max_iters, pix);
 }
 
 foe_status foe_energy_grad(foe_ctx *c, const float *u, const float *data, int H, int W, int ld, foe_model model,

@@ -35,6 +35,7 @@ struct foe_ctx {
     // step-loop timing (foe_profile)
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    cudaGraphExec_t batch_exec = nullptr;   // cached graph of the last captured foe_denoise_batch
     long prof_launches = 0;
     double prof_pixel_iters = 0.0;
     char err[512] = {};
