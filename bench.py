@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--no-train", dest="train", action="store_false",
+                    help="skip the prior-training leg (128 x 180^2, 50 unrolled iterations)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the leg with 64 uneven images in one CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -506,6 +508,38 @@ def main():
                    "iters": "U{100..300} per image", "peaks": "log-U[1, 30]"}
         del bys, bxs, bdescs
 
+    # prior training: 128 pairs of 180x180 at peak 4, 50 checkpointed iterations, loss + gradient per step
+    train = None
+    if args.train:
+        TB, TH, TW, TT = 128, 180, 180, 50
+        tld = (TW + 3) // 4 * 4
+        tk, ta = synth.filter_bank()
+        cl = torch.zeros((TB, TH, tld), dtype=torch.float32, device=dev)
+        nz = torch.zeros((TB, TH, tld), dtype=torch.float32, device=dev)
+        for s_ in range(TB):
+            c_ = synth.clean_image(TH, TW, 20000 + s_ + 1000 * rank)
+            cl[s_, :, :TW] = torch.from_numpy((c_ * 4.0).astype(np.float32)).to(dev)
+            nz[s_, :, :TW] = torch.from_numpy(synth.poisson_observation(c_, 4.0, 21000 + s_ + 1000 * rank)
+                                              .astype(np.float32)).to(dev)
+        dkg = torch.empty((48, 49), dtype=torch.float32, device=dev)
+        dag = torch.empty((48,), dtype=torch.float32, device=dev)
+        topts = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_FP32, iters=TT)
+        F.foe_train_step(ctx, cl, nz, TB, TH, TW, tld, topts, dkg, dag, 0, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tloss = F.foe_train_step(ctx, cl, nz, TB, TH, TW, tld, topts, dkg, dag, 0, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        train = {"images": TB, "H": TH, "W": TW, "iters": TT, "checkpoint_every": 7, "ms_per_step": float(np.median(tt)),
+                 "loss": tloss, "grad_norm": float(torch.linalg.vector_norm(dkg)),
+                 "unrolled_mpix_iter_per_s": TB * TH * TW * TT / (float(np.median(tt)) / 1e3) / 1e6,
+                 "precision": "fp32 forward, recompute and backward"}
+        del cl, nz
+
     # serving leg: continuous batching under a 40 GB budget vs the plain per-request paths
     serve = None
     if args.serve_requests > 0:
@@ -527,7 +561,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "single_image_ms": float(np.median(lat)),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "serve": serve,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "train": train, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -82,6 +82,10 @@ def lib() -> C.CDLL:
             L.orc_denoise.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, _dp]
             L.orc_lipschitz.restype = C.c_double
             L.orc_lipschitz.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int]
+            L.orc_train_loss.restype = C.c_double
+            L.orc_train_loss.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, C.c_int]
+            L.orc_train_grad.restype = C.c_double
+            L.orc_train_grad.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, C.c_int, _dp, _dp]
             L.orc_psnr.restype = C.c_double
             L.orc_psnr.argtypes = [C.c_long, _dp, _dp, C.c_double]
             _lib = L
@@ -230,6 +234,19 @@ class Problem:
         e = np.empty(iters + 1) if trace else None
         lib().orc_ipiano(C.byref(self.p), _p(d), _p(u), _p(up), int(iters), _p(e) if trace else None)
         return (u, up, e) if trace else (u, up)
+
+    def train_loss(self, clean, noisy, T) -> float:
+        """Sum over the batch of 1/2 ||I_C(u^T) - g||^2 (Anscombe quadratic model, T unrolled steps)."""
+        c, y = _d(clean), _d(noisy)
+        return lib().orc_train_loss(C.byref(self.p), c.shape[0], _p(c), _p(y), int(T))
+
+    def train_grad(self, clean, noisy, T):
+        """(loss, dL/dk (nf, 7, 7) in convolution orientation, dL/d log alpha (nf,))."""
+        c, y = _d(clean), _d(noisy)
+        dk = np.empty((self.k.shape[0], 49))
+        da = np.empty(self.k.shape[0])
+        L = lib().orc_train_grad(C.byref(self.p), c.shape[0], _p(c), _p(y), int(T), _p(dk), _p(da))
+        return L, dk.reshape(-1, 7, 7), da
 
     def denoise(self, y, peak, iters, zero_c=0.0):
         y = _d(y)

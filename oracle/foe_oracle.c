@@ -433,3 +433,121 @@ double orc_psnr(long n, const double *a, const double *b, double peak)
     double mse = s / (double)n;
     return 10.0 * log10(255.0 * 255.0 / mse);
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Training (Sec. 2.5, Eq. learningmodel; loss of Sec. 3.2: l = 1/2 ||I_C(u) - g||^2 per image).
+ * The lower-level solve is T unrolled iPiano steps of the Anscombe quadratic model (Eq. overallModel,
+ * prox Eq. subproblemGL2) from u^0 = u^{-1} = v; the parameters are the filters k_i (convolution
+ * orientation) and the log-weights a_i, alpha_i = e^{a_i} (Eq. learningmodel).  The gradient is taken by
+ * reverse-mode differentiation of the unrolled iteration:
+ *   u^{n+1} = c1 (u^n - tau grad F(u^n) + gamma (u^n - u^{n-1})) + c2 v,   c1 = 1/(1+tau lambda),
+ *   gbar^T = I_C'(u^T) (I_C(u^T) - g)   (0 where the output clamp max(u, sqrt(3/2)) is active),
+ *   w = c1 gbar^{n+1},
+ *   gbar^n = (1 + gamma) w - tau H(u^n) w - gamma c1 gbar^{n+2},  H(u) w = sum_i alpha_i K_i^T (rho''(K_i u) K_i w)
+ *            (Hessian of the prior, Sec. 2.5.2),
+ *   dL/da_i     += -tau alpha_i sum_p (K_i w)_p rho'((K_i u^n)_p),
+ *   dL/dk_i(a,b) += -tau alpha_i sum_p [ (P w)(p - (a,b)) rho'(r_i(p)) + (K_i w)_p rho''(r_i(p)) (P u^n)(p - (a,b)) ].
+ * ---------------------------------------------------------------------------------------- */
+static double orc_loss_one(const double *u, const double *g, long N, double *gbar)
+{
+    const double zmin = sqrt(1.5);
+    double L = 0.0;
+    for (long i = 0; i < N; ++i) {
+        const double z = u[i] > zmin ? u[i] : zmin;
+        const double e = orc_ic1(z) - g[i];
+        L += 0.5 * e * e;
+        if (gbar) gbar[i] = u[i] > zmin ? orc_ic_deriv1(u[i]) * e : 0.0;
+    }
+    return L;
+}
+
+/* Runs the T-step forward solve of one image; U receives u^0..u^T ((T+1) x N). */
+static void orc_train_forward(const orc_params *p, const double *y, int T, double *v, double *U)
+{
+    const long N = (long)p->H * p->W;
+    orc_anscombe(N, y, v);
+    memcpy(U, v, sizeof(double) * (size_t)N);
+    for (int n = 0; n < T; ++n)
+        orc_ipiano_step(p, v, U + (size_t)n * N, n == 0 ? v : U + (size_t)(n - 1) * N, U + (size_t)(n + 1) * N);
+}
+
+double orc_train_loss(const orc_params *p, int B, const double *clean, const double *noisy, int T)
+{
+    const long N = (long)p->H * p->W;
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+    double *U = (double *)malloc(sizeof(double) * (size_t)N * (T + 1));
+    if (!v || !U) { free(v); free(U); return NAN; }
+    double L = 0.0;
+    for (int s = 0; s < B; ++s) {
+        orc_train_forward(p, noisy + (size_t)s * N, T, v, U);
+        L += orc_loss_one(U + (size_t)T * N, clean + (size_t)s * N, N, NULL);
+    }
+    free(v);
+    free(U);
+    return L;
+}
+
+double orc_train_grad(const orc_params *p, int B, const double *clean, const double *noisy, int T, double *dk,
+                      double *dlogalpha)
+{
+    const int nf = p->nf, H = p->H, W = p->W;
+    const long N = (long)H * W, PW = W + 2 * ORC_R, PN = (long)(H + 2 * ORC_R) * PW;
+    const double c1 = 1.0 / (1.0 + p->tau * p->lambda);
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+    double *U = (double *)malloc(sizeof(double) * (size_t)N * (T + 1));
+    double *gb1 = (double *)calloc((size_t)N, sizeof(double));   /* gbar^{n+1} */
+    double *gb2 = (double *)calloc((size_t)N, sizeof(double));   /* gbar^{n+2} */
+    double *w = (double *)malloc(sizeof(double) * (size_t)N);
+    double *r = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *sv = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *psi = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *Hw = (double *)malloc(sizeof(double) * (size_t)N);
+    double *pu = (double *)malloc(sizeof(double) * (size_t)PN);
+    double *pw = (double *)malloc(sizeof(double) * (size_t)PN);
+    double L = NAN;
+    if (!v || !U || !gb1 || !gb2 || !w || !r || !sv || !psi || !Hw || !pu || !pw) goto done;
+    for (int i = 0; i < nf * ORC_KK; ++i) dk[i] = 0.0;
+    for (int i = 0; i < nf; ++i) dlogalpha[i] = 0.0;
+    L = 0.0;
+    for (int s = 0; s < B; ++s) {
+        orc_train_forward(p, noisy + (size_t)s * N, T, v, U);
+        L += orc_loss_one(U + (size_t)T * N, clean + (size_t)s * N, N, gb1);
+        for (long i = 0; i < N; ++i) gb2[i] = 0.0;
+        for (int n = T - 1; n >= 0; --n) {
+            const double *un = U + (size_t)n * N;
+            for (long i = 0; i < N; ++i) w[i] = c1 * gb1[i];
+            orc_responses(nf, p->k, H, W, un, p->bc, r, p->nthreads);
+            orc_responses(nf, p->k, H, W, w, p->bc, sv, p->nthreads);
+            orc_pad_image(H, W, un, p->bc, pu);
+            orc_pad_image(H, W, w, p->bc, pw);
+            for (int f = 0; f < nf; ++f) {
+                const double *rf = r + (size_t)f * N, *sf = sv + (size_t)f * N;
+                double ga = 0.0;
+                for (long q = 0; q < N; ++q) ga += sf[q] * orc_rho1(rf[q]);
+                dlogalpha[f] += -p->tau * p->alpha[f] * ga;
+                for (int a = -ORC_R; a <= ORC_R; ++a)
+                    for (int b = -ORC_R; b <= ORC_R; ++b) {
+                        double gk = 0.0;
+                        for (long y = 0; y < H; ++y)
+                            for (long x = 0; x < W; ++x) {
+                                const long q = y * W + x, pi = (y - a + ORC_R) * PW + (x - b + ORC_R);
+                                gk += pw[pi] * orc_rho1(rf[q]) + sf[q] * orc_rho2(rf[q]) * pu[pi];
+                            }
+                        dk[(size_t)f * ORC_KK + (a + ORC_R) * ORC_KS + (b + ORC_R)] += -p->tau * p->alpha[f] * gk;
+                    }
+                for (long q = 0; q < N; ++q) psi[(size_t)f * N + q] = p->alpha[f] * orc_rho2(rf[q]) * sf[q];
+            }
+            if (n >= 1) {
+                orc_adjoint(nf, p->k, H, W, psi, p->bc, Hw, p->nthreads);
+                for (long i = 0; i < N; ++i) {
+                    const double gn = (1.0 + p->gamma) * w[i] - p->tau * Hw[i] - p->gamma * c1 * gb2[i];
+                    gb2[i] = gb1[i];
+                    gb1[i] = gn;
+                }
+            }
+        }
+    }
+done:
+    free(v); free(U); free(gb1); free(gb2); free(w); free(r); free(sv); free(psi); free(Hw); free(pu); free(pw);
+    return L;
+}

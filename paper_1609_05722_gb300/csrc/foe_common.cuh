@@ -54,6 +54,31 @@ struct LaunchArgs {
     ImgDesc img[kMaxBatch];
 };
 
+// Backward pass of the unrolled solve (training): one image of a launch.
+struct BwdImg {
+    const float *u;            // u^n
+    const float *gb1;          // gbar^{n+1}
+    const float *gb2;          // gbar^{n+2} (nullable: zero)
+    float *gout;               // gbar^n
+    int H, W, ld;
+    int tiles_x;
+};
+
+constexpr int kBwdPartials = kNF * kKK + kNF;  // per-tile partial sums: filters (48 x 49), then weights (48)
+
+struct BwdArgs {
+    int nimg;
+    int bc;
+    int nchunks;
+    int write_g;               // 0 at the last reverse step (gbar^0 is not needed)
+    float tau, gamma, c1;      // c1 = 1 / (1 + tau lambda)
+    const float *wts;          // device [48][49], correlation form
+    const float *alpha;        // device [48]
+    float *partials;           // [tiles][kBwdPartials]
+    int tile_prefix[kMaxBatch + 1];
+    BwdImg img[kMaxBatch];
+};
+
 // Half-sample symmetric padding (edge repeated), any overshoot; -1 for zero padding outside.
 __host__ __device__ inline int pad_index(int i, int n, int bc)
 {

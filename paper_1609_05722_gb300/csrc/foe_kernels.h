@@ -20,6 +20,18 @@ size_t tc_smem_bytes();
 cudaError_t tc_setup();
 cudaError_t tc_launch(const LaunchArgs &a, int mode, int *d_status, cudaStream_t s);
 
+// Backward pass of the unrolled solve (foe_train.cu).
+int bwd_tile();
+size_t bwd_smem_bytes();
+cudaError_t bwd_setup();
+cudaError_t bwd_launch(const BwdArgs &a, cudaStream_t s);
+cudaError_t launch_train_loss(const float *u_hi, const float *u_lo, const float *clean, int H, int W, int ld, int cld,
+                              float *gbar, double *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_partials(const float *partials, int tiles, double *acc, cudaStream_t s);
+cudaError_t launch_train_finish(const double *acc, const float *alpha, float tau, int nf, float *dk, float *dla,
+                                cudaStream_t s);
+cudaError_t launch_copy(const float *src, float *dst, long n, cudaStream_t s);
+
 cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model, float zero_c, float *d, float *uh,
                         float *ul, float *delta, cudaStream_t s);
 cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x,

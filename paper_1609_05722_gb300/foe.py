@@ -33,7 +33,7 @@ class foe_prior(C.Structure):
 class foe_solve_opts(C.Structure):
     _fields_ = [("model", C.c_int), ("lam", C.c_float), ("gamma", C.c_float), ("tau", C.c_float),
                 ("tol", C.c_float), ("iters", C.c_int), ("step", C.c_int), ("bc", C.c_int),
-                ("prec", C.c_int), ("zero_c", C.c_float)]
+                ("prec", C.c_int), ("zero_c", C.c_float), ("use_graph", C.c_int)]
 
 
 class foe_report(C.Structure):
@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
             "foe_server_tick": (i, [vp, C.POINTER(i)]),
             "foe_server_poll": (i, [vp, C.POINTER(C.c_longlong), i, C.POINTER(i)]),
             "foe_server_get_stats": (i, [vp, C.POINTER(foe_server_stats)]),
+            "foe_train_step": (i, [vp, vp, vp, i, i, i, i, C.POINTER(foe_solve_opts), i, C.POINTER(d), vp, vp, vp]),
             "foe_profile": (i, [vp, i]),
             "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
             "foe_status_string": (C.c_char_p, [i]),
@@ -154,16 +155,18 @@ class SolveOpts:
     bc: int = FOE_BC_SYMMETRIC
     prec: int = FOE_PREC_BF16
     zero_c: float = 0.0
+    use_graph: bool = False
 
     def c(self) -> foe_solve_opts:
         return foe_solve_opts(self.model, self.lam, self.gamma, self.tau, self.tol, self.iters, self.step,
-                              self.bc, self.prec, self.zero_c)
+                              self.bc, self.prec, self.zero_c, 1 if self.use_graph else 0)
 
 
 def foe_default_opts() -> SolveOpts:
     o = foe_solve_opts()
     _check(lib().foe_default_opts(C.byref(o)))
-    return SolveOpts(o.model, o.lam, o.gamma, o.tau, o.tol, o.iters, o.step, o.bc, o.prec, o.zero_c)
+    return SolveOpts(o.model, o.lam, o.gamma, o.tau, o.tol, o.iters, o.step, o.bc, o.prec, o.zero_c,
+                     bool(o.use_graph))
 
 
 def _prior(filters, alpha):
@@ -311,3 +314,13 @@ def foe_server_get_stats(srv) -> dict:
     s = foe_server_stats()
     _check(lib().foe_server_get_stats(srv, C.byref(s)), what="foe_server_get_stats")
     return {k: getattr(s, k) for k, _ in foe_server_stats._fields_}
+
+
+def foe_train_step(ctx, clean, noisy, B: int, H: int, W: int, ld: int, opts: SolveOpts, dfilters, dlogalpha,
+                   ckpt_every: int = 0, stream=None) -> float:
+    """Loss and gradients of the unrolled solve (see include/foe.h); returns the loss."""
+    loss = C.c_double()
+    o = opts.c()
+    _check(lib().foe_train_step(ctx, _ptr(clean), _ptr(noisy), B, H, W, ld, C.byref(o), ckpt_every, C.byref(loss),
+                                _ptr(dfilters), _ptr(dlogalpha), _stream(stream)), ctx, "foe_train_step")
+    return loss.value

@@ -346,3 +346,37 @@ def test_denoise_model_selection_and_pipeline(bank):
 def test_psnr_closed_form():
     a = np.full(100, 2.0)
     assert O.psnr(a + 0.1, a, 4.0) == pytest.approx(20 * math.log10(4.0 / 0.1), rel=1e-12)
+
+
+# ----------------------------------------------------------------- training gradient (Sec. 2.5, 3.2)
+
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_training_gradient_matches_central_differences(bank, bc):
+    # Reverse-mode gradient of sum_s 1/2 ||I_C(u_s^T) - g_s||^2 through T unrolled steps against central
+    # finite differences (eps = 1e-3, FP64) along random directions in (filters, log-weights).
+    k, a = bank
+    k, a = k[:6].copy(), a[:6].copy()
+    H, W, T, B = 11, 9, 5, 2
+    rng = np.random.default_rng(21)
+    clean = np.stack([synth.clean_image(H, W, 30 + s) * 4.0 for s in range(B)])
+    noisy = np.stack([synth.poisson_observation(clean[s] / 4.0, 4.0, 40 + s) for s in range(B)])
+    tau = 0.02
+    pr = O.Problem(k, a, H, W, bc=bc, model=O.MODEL_ANS_L2, lam=1.3, tau=tau, gamma=0.7, nthreads=1)
+    L, dk, da = pr.train_grad(clean, noisy, T)
+    assert L == pytest.approx(pr.train_loss(clean, noisy, T), rel=1e-14)
+    eps = 1e-3
+    for _ in range(3):
+        dkd = rng.standard_normal(k.shape)
+        dad = rng.standard_normal(a.shape)
+        nrm = np.sqrt((dkd ** 2).sum() + (dad ** 2).sum())  # unit direction: the step is eps in parameter norm
+        dkd, dad = dkd / nrm, dad / nrm
+        def loss_at(t):
+            q = O.Problem(k + t * dkd, a * np.exp(t * dad), H, W, bc=bc, model=O.MODEL_ANS_L2, lam=1.3, tau=tau,
+                          gamma=0.7, nthreads=1)
+            return q.train_loss(clean, noisy, T)
+        fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
+        fd2 = (loss_at(eps / 2) - loss_at(-eps / 2)) / eps
+        rich = (4 * fd2 - fd) / 3  # Richardson: removes the O(eps^2) truncation error of the central difference
+        an = float((dk * dkd).sum() + (da * dad).sum())
+        assert an == pytest.approx(fd, rel=1e-4, abs=1e-9)
+        assert an == pytest.approx(rich, rel=1e-6, abs=1e-10)
