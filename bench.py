@@ -39,6 +39,26 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (the timing rule: the job is as slow as its slowest rank)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput in units per second: every rank processes its own equal share (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seeds of rank r's synthetic inputs: distinct per rank so replicas never denoise the same images."""
+    return base + 100 * rank
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -103,9 +123,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
+KERNEL_SOURCES = {"foe_tc_step": ("foe_tc.cu", "foe_common.cuh"), "foe_f32_step": ("foe_f32.cu", "foe_common.cuh")}
+
+
+def kernel_source_sha(kernel_key: str) -> str:
+    """Hash of the sources of one kernel: an ncu figure is only used while they are unchanged."""
     h = hashlib.sha256()
-    for name in ("foe_tc.cu", "foe_f32.cu", "foe_common.cuh"):
+    for name in KERNEL_SOURCES[kernel_key]:
         with open(os.path.join(ROOT, "paper_1609_05722_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -119,7 +143,7 @@ def ncu_traffic(kernel_key: str):
     with open(p) as f:
         t = json.load(f)
     e = t.get(kernel_key)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel_key):
         return None
     return e.get("bytes_per_launch")
 
@@ -335,7 +359,7 @@ def main():
     ys_host, ys, xs = [], [], []
     for mi, model in enumerate((F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2)):
         for pi, peak in enumerate(PEAKS):
-            seed = 1000 + 10 * pi + 100 * rank
+            seed = rank_seed(1000 + 10 * pi, rank)
             y = synth.poisson_observation(synth.clean_image(H, W, seed), peak, seed + 5000).astype(np.float32)
             yh = torch.from_numpy(y).pin_memory()
             ys_host.append(yh)
@@ -372,9 +396,7 @@ def main():
         loop_ms, launches, pix = F.foe_profile_read(ctx)
         torch.cuda.synchronize()
         if world > 1:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = max_over_ranks(total, dist, dev)
             dist.barrier()
         return total, loop_ms, launches, pix
 
@@ -393,7 +415,7 @@ def main():
     total_ms, loop_ms, launches, pix = timed(prec_main, args.steps, args.warmup)
     clocks = sampler.stop()
     pix_iters_step = 10 * H * W * ITERS
-    value = world * pix_iters_step * args.steps / (total_ms / 1e3) / 1e6
+    value = job_value(pix_iters_step * args.steps, total_ms / 1e3, world) / 1e6
     ms_per_step = total_ms / args.steps
 
     # roofline of the fused step kernel (average launch = step-loop device time / launches)
@@ -467,10 +489,8 @@ def main():
         e2e_step()
     t_e2e = time.perf_counter() - t0
     if world > 1:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * pix_iters_step * args.steps / t_e2e / 1e6, "unit": "MPix·iter/s",
+        t_e2e = max_over_ranks(t_e2e, dist, dev)
+    e2e = {"value": job_value(pix_iters_step * args.steps, t_e2e, world) / 1e6, "unit": "MPix·iter/s",
            "h2d_bytes_per_step": 10 * H * W * 4, "d2h_bytes_per_step": 10 * H * ld * 4}
 
     # batched uneven instances in one graph: 64 images, sides {128..1024}, peaks log-U[1, 30], 100-300 iters
