@@ -452,6 +452,13 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    # TF32 tensor-core convolutions on the same workload (the third precision of the comparison)
+    tf32 = None
+    if prec_main == F.FOE_PREC_BF16 and args.fp32_steps > 0:
+        t3, l3, n3, p3 = timed(F.FOE_PREC_TF32, args.fp32_steps, 1)
+        tf32 = {"value": job_value(pix_iters_step * args.fp32_steps, t3 / 1e3, world) / 1e6, "unit": "MPix·iter/s",
+                "ms_per_step": t3 / args.fp32_steps, "avg_launch_us": (l3 / 1e3) / max(n3, 1) * 1e6}
+
     # single-image latency (one 512x512 image, 300 iterations, A2 model at peak 8)
     xs1 = torch.empty((H, ld), dtype=torch.float32, device=dev)
     for _ in range(2):
@@ -580,7 +587,7 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded images, DCT-7 filter bank)",
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-                "fp32_plain": fp32, "single_image_ms": float(np.median(lat)),
+                "fp32_plain": fp32, "tf32_tensor_core": tf32, "single_image_ms": float(np.median(lat)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "train": train, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)

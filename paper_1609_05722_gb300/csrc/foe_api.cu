@@ -127,10 +127,13 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         return s;
     };
     const std::vector<uint16_t> ops = tc_operands(w, c->alpha);
+    const std::vector<uint32_t> ops32 = tc_operands_tf32(w, c->alpha);
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_wts, sizeof(w))) || (e = cudaMalloc(&c->d_alpha, sizeof(c->alpha))) ||
         (e = cudaMalloc(&c->d_tcops, ops.size() * sizeof(uint16_t))) ||
         (e = cudaMemcpy(c->d_tcops, ops.data(), ops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice)) ||
+        (e = cudaMalloc(&c->d_tcops32, ops32.size() * sizeof(uint32_t))) ||
+        (e = cudaMemcpy(c->d_tcops32, ops32.data(), ops32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) ||
         (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) ||
         (e = cudaMemcpy(c->d_wts, w, sizeof(w), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
@@ -149,6 +152,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_wts);
     cudaFree(c->d_alpha);
     cudaFree(c->d_tcops);
+    cudaFree(c->d_tcops32);
     cudaFree(c->d_energy);
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
@@ -307,7 +311,10 @@ foe_status foe_energy_grad(foe_ctx *c, const float *u, const float *data, int H,
     }
     if (!(lambda > 0.0f)) { set_err(c, "lambda must be > 0"); return FOE_EINVAL; }
     if (bc != FOE_BC_SYMMETRIC && bc != FOE_BC_ZERO) { set_err(c, "bad bc"); return FOE_EINVAL; }
-    if (prec != FOE_PREC_FP32 && prec != FOE_PREC_BF16) { set_err(c, "precision not supported"); return FOE_EUNSUPPORTED; }
+    if (prec != FOE_PREC_FP32 && prec != FOE_PREC_BF16 && prec != FOE_PREC_TF32) {
+        set_err(c, "bad precision");
+        return FOE_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     ImgDesc d{};
     d.u_hi[0] = const_cast<float *>(u);
@@ -360,7 +367,10 @@ foe_status foe_ipiano_step(foe_ctx *c, const float *u_hi, float *u_lo, float *de
         return FOE_EINVAL;
     }
     if (bc != FOE_BC_SYMMETRIC && bc != FOE_BC_ZERO) { set_err(c, "bad bc"); return FOE_EINVAL; }
-    if (prec != FOE_PREC_FP32 && prec != FOE_PREC_BF16) { set_err(c, "precision not supported"); return FOE_EUNSUPPORTED; }
+    if (prec != FOE_PREC_FP32 && prec != FOE_PREC_BF16 && prec != FOE_PREC_TF32) {
+        set_err(c, "bad precision");
+        return FOE_EINVAL;
+    }
     ImgDesc e{};
     e.u_hi[0] = const_cast<float *>(u_hi);
     e.u_hi[1] = u_next_hi;

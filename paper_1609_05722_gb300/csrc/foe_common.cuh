@@ -50,6 +50,7 @@ struct LaunchArgs {
     const float *alpha;        // device [48]
     double *partials;          // kEnergy: one FP64 partial per tile
     const void *tcops;         // tensor-core operand images (bf16): forward filters, then adjoint filters
+    const void *tcops32;       // the same images in tf32
     int tile_prefix[kMaxBatch + 1];
     ImgDesc img[kMaxBatch];
 };

@@ -25,6 +25,7 @@ struct foe_ctx {
     float *d_wts = nullptr;                 // device [48][49], correlation orientation
     float *d_alpha = nullptr;               // device [48]
     void *d_tcops = nullptr;                // device, bf16 operand images of the tensor-core kernel (12 KB)
+    void *d_tcops32 = nullptr;              // device, the same in tf32 (24 KB)
     void *ws = nullptr;
     size_t ws_bytes = 0;
     double *d_partials = nullptr;
@@ -123,6 +124,38 @@ inline std::vector<uint16_t> tc_operands(const float *w, const float *alpha)
     return out;
 }
 
+inline uint32_t f32_to_tf32_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);  // round to nearest even at 10 mantissa bits (inputs are finite)
+    return u & ~0x1FFFu;
+}
+
+// tf32 operand images (32-bit containers), 4 values per 16-byte entry:
+//   forward B  [tap row a (8)][column chunk (2)][filter (48)][tap cols 4c..4c+3] = w_f(a, b)  (0 for a or b = 7)
+//   adjoint B  [filter chunk (12)][tap 8a+b (64)][filters 4c..4c+3] = 2 alpha_f w_f(a, b)
+inline std::vector<uint32_t> tc_operands_tf32(const float *w, const float *alpha)
+{
+    std::vector<uint32_t> out(8 * 2 * 48 * 4 + 12 * 64 * 4, 0);
+    for (int a = 0; a < 8; ++a)
+        for (int ch = 0; ch < 2; ++ch)
+            for (int f = 0; f < 48; ++f)
+                for (int e = 0; e < 4; ++e) {
+                    const int b = 4 * ch + e;
+                    out[((a * 2 + ch) * 48 + f) * 4 + e] = (a < 7 && b < 7) ? f32_to_tf32_bits(w[f * foe::kKK + a * 7 + b]) : 0;
+                }
+    uint32_t *adj = out.data() + 8 * 2 * 48 * 4;
+    for (int ch = 0; ch < 12; ++ch)
+        for (int n = 0; n < 64; ++n)
+            for (int e = 0; e < 4; ++e) {
+                const int f = 4 * ch + e, a = n / 8, b = n % 8;
+                adj[(ch * 64 + n) * 4 + e] =
+                    (a < 7 && b < 7) ? f32_to_tf32_bits(2.0f * alpha[f] * w[f * foe::kKK + a * 7 + b]) : 0;
+            }
+    return out;
+}
+
 inline foe_status check_prior(const foe_prior *p)
 {
     if (!p || !p->filters || !p->alpha) return FOE_EINVAL;
@@ -156,7 +189,6 @@ inline foe_status check_opts(foe_ctx *c, const foe_solve_opts *o)
         set_err(c, "bad precision");
         return FOE_EINVAL;
     }
-    if (o->prec == FOE_PREC_TF32) { set_err(c, "TF32 convolutions are not implemented"); return FOE_EUNSUPPORTED; }
     if (!(o->zero_c >= 0.0f) || !std::isfinite(o->zero_c)) { set_err(c, "zero_c must be >= 0"); return FOE_EINVAL; }
     return FOE_OK;
 }
@@ -191,7 +223,7 @@ inline foe::StepConsts step_consts(float tau, float gamma, float lambda)
 
 inline void tile_dims(int prec, int &th, int &tw)
 {
-    if (prec == FOE_PREC_BF16) {
+    if (prec == FOE_PREC_BF16 || prec == FOE_PREC_TF32) {
         th = foe::tc_tile_h();
         tw = foe::tc_tile_w();
     } else {
@@ -210,6 +242,7 @@ inline void args_begin(foe_ctx *c, int bc)
     A.alpha = c->d_alpha;
     A.partials = c->d_partials;
     A.tcops = c->d_tcops;
+    A.tcops32 = c->d_tcops32;
     A.tile_prefix[0] = 0;
 }
 
@@ -228,7 +261,8 @@ inline void args_add(foe_ctx *c, int prec, const ImgDesc &d)
 
 inline foe_status launch(foe_ctx *c, int prec, int mode, cudaStream_t s)
 {
-    cudaError_t e = prec == FOE_PREC_BF16 ? foe::tc_launch(c->args, mode, c->d_status, s) : foe::f32_launch(c->args, mode, s);
+    cudaError_t e = prec == FOE_PREC_FP32 ? foe::f32_launch(c->args, mode, s)
+                                          : foe::tc_launch(c->args, mode, prec == FOE_PREC_TF32, c->d_status, s);
     if (e != cudaSuccess) {
         set_err(c, "kernel launch failed: %s", cudaGetErrorString(e));
         return e == cudaErrorNotSupported ? FOE_EUNSUPPORTED : FOE_ECUDA;

@@ -13,12 +13,12 @@ size_t f32_smem_bytes();
 cudaError_t f32_setup();
 cudaError_t f32_launch(const LaunchArgs &a, int mode, cudaStream_t s);
 
-// Tensor-core (tcgen05, BF16) fused tile kernel (foe_tc.cu).
+// Tensor-core (tcgen05, BF16 or TF32) fused tile kernel (foe_tc.cu).
 int tc_tile_h();
 int tc_tile_w();
 size_t tc_smem_bytes();
 cudaError_t tc_setup();
-cudaError_t tc_launch(const LaunchArgs &a, int mode, int *d_status, cudaStream_t s);
+cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s);
 
 // Backward pass of the unrolled solve (foe_train.cu).
 int bwd_tile();

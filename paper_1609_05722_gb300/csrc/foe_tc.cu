@@ -1,5 +1,5 @@
-// Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, FP32 accumulators in
-// tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
+// Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, kind::f16, or TF32 operands,
+// kind::tf32; FP32 accumulators in tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
 //
 // One CTA owns a 26x26 output tile.  The prior gradient sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF)
 // needs the responses on the tile plus a 3-pixel ring: a 32x32 response region, processed as 8
@@ -50,11 +50,26 @@ constexpr int LAG = 2;                 // the adjoint of M-tile g is issued, and
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
+// Operand images in shared memory.  BF16: 16-byte entries of 8 values.  TF32: 16-byte entries of 4 values,
+// so every 8-value K-chunk of the BF16 layout becomes two chunks (E is split into E[0] = u(x..x+3) and
+// E[1] = u(x+4..x+7); the descriptor's leading offset steps from one half to the other).
+template <bool TF>
+struct TcOps;
+template <>
+struct TcOps<false> {
+    static constexpr int EB = 1, WF = 8 * 48, WA = 6 * 64, PSI = 6 * 128;
+};
+template <>
+struct TcOps<true> {
+    static constexpr int EB = 2, WF = 8 * 2 * 48, WA = 12 * 64, PSI = 12 * 128;
+};
+
+template <bool TF>
 struct TcSmem {
-    uint4 E[EROWS * RS];        // forward A operand: entry (row, x) = 8 bf16 of u(row, x..x+7)
-    uint4 Wf[8 * 48];           // forward B operand [tap row a][filter][tap col b]
-    uint4 Wa[6 * 64];           // adjoint B operand [filter group][tap 8a+b][filter in group]
-    uint4 Psi[NPSI][6 * 128];   // adjoint A operand [buffer][filter group][pixel][filter in group]
+    uint4 E[TcOps<TF>::EB][EROWS * RS];   // forward A operand: entry (row, x) holds u(row, x..x+7)
+    uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
+    uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
+    uint4 Psi[NPSI][TcOps<TF>::PSI];       // adjoint A operand [buffer][filter chunk][pixel][filters in chunk]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
     float U[UR * UC];           // fp32 input region
     float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
@@ -138,6 +153,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N)
+{
+    // D FP32 (bit 4), A TF32 (bits 7-9 = 2), B TF32 (bits 10-12 = 2), both K-major.
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t d;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(d) : "f"(x));
+    return d;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -190,7 +228,8 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 // Sum of the horizontal partials at (qy, qx) of the response region over the 7 tap rows; rows and
 // columns outside the region are outside the image whenever they are asked for, so they add 0.
-__device__ __forceinline__ float hs_gather(const TcSmem &S, int qy, int qx)
+template <bool TF>
+__device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
 {
     if (qx < 0 || qx >= RS) return 0.0f;
     float g = 0.0f;
@@ -202,11 +241,11 @@ __device__ __forceinline__ float hs_gather(const TcSmem &S, int qy, int qx)
     return g;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
+template <int MODE, bool TF>
+__global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+    TcSmem<TF> &S = *reinterpret_cast<TcSmem<TF> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x;
     const int im = tile_image(A, tile);
@@ -223,8 +262,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     __syncthreads();
 
     // ---- asynchronous staging: group 0 = input region + filter images, group 1 = output-pass operands ----
-    const uint4 *ops = reinterpret_cast<const uint4 *>(A.tcops);
-    for (int j = tid; j < 8 * 48 + 6 * 64; j += NTHR) cp_async16(j < 8 * 48 ? &S.Wf[j] : &S.Wa[j - 8 * 48], ops + j);
+    constexpr int NWF = TcOps<TF>::WF, NWA = TcOps<TF>::WA;
+    const uint4 *ops = reinterpret_cast<const uint4 *>(TF ? A.tcops32 : A.tcops);
+    for (int j = tid; j < NWF + NWA; j += NTHR) cp_async16(j < NWF ? &S.Wf[j] : &S.Wa[j - NWF], ops + j);
     if (tid < UR) S.srow[tid] = pad_index(oy0 - 6 + tid, H, A.bc);
     else if (tid < 2 * UR) S.scol[tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
     __syncthreads();
@@ -286,12 +326,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     for (int j = tid; j < EROWS * RS; j += NTHR) {
         const int i = j / RS, x = j % RS;
         const float *src = &S.U[i * UC + x];
-        uint4 e;
-        e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
-        e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
-        e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
-        e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
-        S.E[j] = e;
+        if (TF) {
+            S.E[0][j] = make_uint4(to_tf32(src[0] - mean), to_tf32(src[1] - mean), to_tf32(src[2] - mean),
+                                   to_tf32(src[3] - mean));
+            S.E[TcOps<TF>::EB - 1][j] = make_uint4(to_tf32(src[4] - mean), to_tf32(src[5] - mean),
+                                                   to_tf32(src[6] - mean), to_tf32(src[7] - mean));
+        } else {
+            uint4 e;
+            e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
+            e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
+            e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
+            e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
+            S.E[0][j] = e;
+        }
     }
     fence_async_smem();
     fence_before();
@@ -303,8 +350,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     if (warp == MMA_WARP) {
         if (lane == 0) {
             // ---------------- MMA issue ----------------
-            constexpr uint32_t IDF = idesc_bf16(128, 48), IDA = idesc_bf16(128, 64);
-            const uint32_t e0 = smem_u32(S.E), wf0 = smem_u32(S.Wf), wa0 = smem_u32(S.Wa);
+            constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
+            constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
+            const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
+            const uint32_t wf0 = smem_u32(S.Wf), wa0 = smem_u32(S.Wa);
             bool ok = true;
             // stage s = t % NSTAGE holds R(t) (columns 64 s .. 64 s + 47) until the epilogue has read it, then
             // the adjoint writes Z(t) over it (64 columns); the stage is free again once Z(t) has been read.
@@ -313,10 +362,18 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 if (!mbar_wait(&S.bar[B_PSI + s], k & 1, abort_flag, status)) return false;
                 fence_after();
                 const uint32_t ps = smem_u32(S.Psi[t % NPSI]);
+                if (TF) {
+                    // K = 48 filters in 6 steps of 8 (two 4-filter chunks each)
 #pragma unroll
-                for (int kk = 0; kk < 3; ++kk)
-                    mma_bf16(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128), sdesc(wa0 + kk * 2 * 1024, 1024, 128),
-                             IDA, kk > 0);
+                    for (int kk = 0; kk < 6; ++kk)
+                        mma_tf32(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128),
+                                 sdesc(wa0 + kk * 2 * 1024, 1024, 128), IDA, kk > 0);
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk)
+                        mma_bf16(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128),
+                                 sdesc(wa0 + kk * 2 * 1024, 1024, 128), IDA, kk > 0);
+                }
                 mma_commit(&S.bar[B_ADJ + s]);
                 return true;
             };
@@ -324,10 +381,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 const int s = t % NSTAGE, k = t / NSTAGE;
                 if (t >= NSTAGE && !mbar_wait(&S.bar[B_ZEMPTY + s], (k - 1) & 1, abort_flag, status)) { ok = false; break; }
                 fence_after();
+                if (TF) {
+                    // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has zero
+                    // weights and is skipped
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    mma_bf16(tmem + 64 * s, sdesc(e0 + (4 * t + 2 * kk) * RS * 16, RS * 16, 128),
-                             sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
+                    for (int kk = 0; kk < 7; ++kk)
+                        mma_tf32(tmem + 64 * s, sdesc(e0 + (4 * t + kk) * RS * 16, e1 - e0, 128),
+                                 sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(tmem + 64 * s, sdesc(e0 + (4 * t + 2 * kk) * RS * 16, RS * 16, 128),
+                                 sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
+                }
                 mma_commit(&S.bar[B_FWD + s]);
                 if (t >= LAG && !adjoint(t - LAG)) ok = false;
             }
@@ -401,17 +467,31 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             fence_before();
             const int gy = oy0 - 3 + 4 * t + q, gx = ox0 - 3 + lane;
             const bool in = interior || (gy >= 0 && gy < H && gx >= 0 && gx < W);
-            uint32_t w[12];
+            if (TF) {
+                uint32_t w[24];
 #pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                const float r0 = r[2 * j], r1 = r[2 * j + 1];
-                const float p0 = r0 * rcp_approx(fmaf(r0, r0, 1.0f));
-                const float p1 = r1 * rcp_approx(fmaf(r1, r1, 1.0f));
-                w[j] = in ? pack_bf16x2(p0, p1) : 0u;
+                for (int j = 0; j < 24; ++j) {
+                    const float r0 = r[j];
+                    w[j] = in ? to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) : 0u;
+                }
+                uint4 *dst = &S.Psi[t % NPSI][(6 * half) * 128 + m];
+#pragma unroll
+                for (int kc = 0; kc < 6; ++kc)
+                    dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+            } else {
+                uint32_t w[12];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    const float r0 = r[2 * j], r1 = r[2 * j + 1];
+                    const float p0 = r0 * rcp_approx(fmaf(r0, r0, 1.0f));
+                    const float p1 = r1 * rcp_approx(fmaf(r1, r1, 1.0f));
+                    w[j] = in ? pack_bf16x2(p0, p1) : 0u;
+                }
+                uint4 *dst = &S.Psi[t % NPSI][(3 * half) * 128 + m];
+#pragma unroll
+                for (int kc = 0; kc < 3; ++kc)
+                    dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
             }
-            uint4 *dst = &S.Psi[t % NPSI][(3 * half) * 128 + m];
-#pragma unroll
-            for (int kc = 0; kc < 3; ++kc) dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
             fence_async_smem();
             mbar_arrive(&S.bar[B_PSI + b]);  // R(t) has been read and Psi(t) written: the adjoint may overwrite the stage
             if (t >= LAG && !col2im(t - LAG)) { ok = false; break; }
@@ -461,23 +541,30 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 
 int tc_tile_h() { return TO; }
 int tc_tile_w() { return TO; }
-size_t tc_smem_bytes() { return sizeof(TcSmem); }
+size_t tc_smem_bytes() { return sizeof(TcSmem<false>); }
 
 cudaError_t tc_setup()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem))))
-        return e;
-    return cudaFuncSetAttribute(k_foe_tc<kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    const int b16 = (int)sizeof(TcSmem<false>), t32 = (int)sizeof(TcSmem<true>);
+    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
+    if ((e = cudaFuncSetAttribute(k_foe_tc<kGrad, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
+    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32))) return e;
+    return cudaFuncSetAttribute(k_foe_tc<kGrad, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32);
 }
 
-cudaError_t tc_launch(const LaunchArgs &a, int mode, int *d_status, cudaStream_t s)
+cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s)
 {
     const int tiles = a.tile_prefix[a.nimg];
     if (tiles <= 0) return cudaSuccess;
-    if (mode == kStep) k_foe_tc<kStep><<<tiles, NTHR, sizeof(TcSmem), s>>>(a, d_status);
-    else if (mode == kGrad) k_foe_tc<kGrad><<<tiles, NTHR, sizeof(TcSmem), s>>>(a, d_status);
-    else return cudaErrorNotSupported;
+    if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
+    if (tf32) {
+        if (mode == kStep) k_foe_tc<kStep, true><<<tiles, NTHR, sizeof(TcSmem<true>), s>>>(a, d_status);
+        else k_foe_tc<kGrad, true><<<tiles, NTHR, sizeof(TcSmem<true>), s>>>(a, d_status);
+    } else {
+        if (mode == kStep) k_foe_tc<kStep, false><<<tiles, NTHR, sizeof(TcSmem<false>), s>>>(a, d_status);
+        else k_foe_tc<kGrad, false><<<tiles, NTHR, sizeof(TcSmem<false>), s>>>(a, d_status);
+    }
     return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
-"""Tensor-core (tcgen05, BF16 operands, FP32 accumulation) path vs the FP64 oracle.
+"""Tensor-core (tcgen05, BF16 or TF32 operands, FP32 accumulation) paths vs the FP64 oracle.
 
-Tolerances follow from the arithmetic: u, the filters and psi are rounded to BF16 (relative 2^-9),
-so one gradient differs from the exact one by at most a few 1e-3 of its scale; a whole solve is
-held to the metric's bar, |PSNR(tc) - PSNR(oracle)| <= 0.02 dB against the clean image.
+Tolerances follow from the arithmetic: u, the filters and psi are rounded to BF16 (relative 2^-9) or
+TF32 (2^-11), so one gradient differs from the exact one by at most a few 1e-3 of its scale (BF16);
+a whole solve is held to the metric's bar, |PSNR(tc) - PSNR(oracle)| <= 0.02 dB against the clean
+image.
 """
 import json
 import os
@@ -23,6 +24,8 @@ F32 = np.float32
 GAMMA = float(F32(0.8))
 LAM = 1.0
 BF16 = F.FOE_PREC_BF16
+TF32 = F.FOE_PREC_TF32
+TC_PRECS = [BF16, TF32]
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_512.json")
 
 
@@ -71,10 +74,11 @@ def problem(bank32, H, W, model, bc, tau):
 SHAPES = [(64, 64), (13, 17), (37, 70), (96, 33), (7, 7), (130, 200)]
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bc", [F.FOE_BC_SYMMETRIC, F.FOE_BC_ZERO])
 @pytest.mark.parametrize("model", [F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2])
-def test_tc_gradient(dev, ctx, bank32, shape, bc, model):
+def test_tc_gradient(dev, ctx, bank32, shape, bc, model, prec):
     H, W = shape
     y = synth.poisson_observation(synth.clean_image(H, W, 40 + H), 6.0, 41 + W)
     d = y if model == F.FOE_MODEL_DIRECT else O.anscombe(y)
@@ -84,18 +88,20 @@ def test_tc_gradient(dev, ctx, bank32, shape, bc, model):
     _, g_ref = problem(bank32, H, W, model, bc, 1e-3).energy_grad(u, d32)
     ud, dd = to_dev(u, dev), to_dev(d32, dev)
     gd = torch.zeros_like(ud)
-    F.foe_energy_grad(ctx, ud, dd, H, W, ud.shape[1], model, LAM, bc, BF16, grad=gd, energy=False)
+    F.foe_energy_grad(ctx, ud, dd, H, W, ud.shape[1], model, LAM, bc, prec, grad=gd, energy=False)
     g = from_dev(gd, W)
     scale = np.abs(g_ref).max()
     err = np.abs(g - g_ref).max() / scale
     rms = np.sqrt(((g - g_ref) ** 2).mean()) / np.sqrt((g_ref ** 2).mean())
-    print(f"tc grad {shape} bc={bc} model={model}: max rel {err:.2e} rms rel {rms:.2e}")
-    assert err <= 2e-2 and rms <= 5e-3
+    print(f"tc grad prec={prec} {shape} bc={bc} model={model}: max rel {err:.2e} rms rel {rms:.2e}")
+    # BF16 operands: 8-bit mantissa; TF32: 10-bit mantissa (errors about 4x smaller)
+    assert err <= (2e-2 if prec == BF16 else 5e-3) and rms <= (5e-3 if prec == BF16 else 1.5e-3)
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("shape", [(64, 64), (37, 70), (7, 7)])
 @pytest.mark.parametrize("model", [F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2, F.FOE_MODEL_ANS_IDIV])
-def test_tc_single_step(dev, ctx, bank32, shape, model):
+def test_tc_single_step(dev, ctx, bank32, shape, model, prec):
     H, W = shape
     bc = F.FOE_BC_SYMMETRIC
     tau, _ = F.foe_step_size(ctx, bc, GAMMA)
@@ -110,26 +116,27 @@ def test_tc_single_step(dev, ctx, bank32, shape, model):
     _, g_ref = pr.energy_grad(u, d32)
     uh, dl, dd = to_dev(u, dev), to_dev(delta, dev), to_dev(d32, dev)
     ul, un = torch.zeros_like(uh), torch.zeros_like(uh)
-    F.foe_ipiano_step(ctx, uh, ul, dl, dd, un, H, W, uh.shape[1], model, LAM, tau, GAMMA, bc, BF16)
+    F.foe_ipiano_step(ctx, uh, ul, dl, dd, un, H, W, uh.shape[1], model, LAM, tau, GAMMA, bc, prec)
     torch.cuda.synchronize()
     got = from_dev(un, W) + from_dev(ul, W)
     assert np.abs(got - ref).max() <= tau * 2e-2 * np.abs(g_ref).max()
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("model,peak", [(F.FOE_MODEL_ANS_L2, 4.0), (F.FOE_MODEL_DIRECT, 4.0),
                                         (F.FOE_MODEL_ANS_IDIV, 2.0), (F.FOE_MODEL_AUTO, 8.0)])
-def test_tc_denoise_64x64_psnr(dev, ctx, bank32, model, peak):
+def test_tc_denoise_64x64_psnr(dev, ctx, bank32, model, peak, prec):
     H = W = 64
     clean = synth.clean_image(H, W, 1000) * peak
     y = synth.poisson_observation(clean / peak, peak, 5000)
     tau, _ = F.foe_step_size(ctx, F.FOE_BC_SYMMETRIC, GAMMA)
     yd = to_dev(y, dev)
     xd = torch.zeros_like(yd)
-    F.foe_denoise(ctx, yd, xd, H, W, yd.shape[1], peak, F.SolveOpts(model=model, iters=100, prec=BF16, tau=tau))
+    F.foe_denoise(ctx, yd, xd, H, W, yd.shape[1], peak, F.SolveOpts(model=model, iters=100, prec=prec, tau=tau))
     x = from_dev(xd, W)
     ref, _ = problem(bank32, H, W, model, F.FOE_BC_SYMMETRIC, tau).denoise(y, peak, 100)
     dp = abs(O.psnr(x, clean, peak) - O.psnr(ref, clean, peak))
-    print(f"tc 64x64 model={model} peak={peak}: dPSNR {dp:.4f} dB, PSNR(x vs oracle) {O.psnr(x, ref, peak):.1f} dB")
+    print(f"tc 64x64 prec={prec} model={model} peak={peak}: dPSNR {dp:.4f} dB, PSNR(x vs oracle) {O.psnr(x, ref, peak):.1f} dB")
     assert dp <= 0.02
 
 
@@ -165,15 +172,17 @@ def test_tc_512_psnr_vs_oracle(dev, ctx, bank32, case):
         xs_ref = ref.ravel()[np.array(g["sample_index"])]
     yd = to_dev(y, dev)
     out = {}
-    for prec in (BF16, F.FOE_PREC_FP32):
+    for prec in (BF16, TF32, F.FOE_PREC_FP32):
         xd = torch.zeros_like(yd)
         F.foe_denoise(ctx, yd, xd, H, W, yd.shape[1], peak,
                       F.SolveOpts(model=model, iters=g["iters"], prec=prec, tau=g["tau"], gamma=GAMMA))
         out[prec] = from_dev(xd, W)
     dp = abs(O.psnr(out[BF16], clean, peak) - psnr_ref)
+    dp32 = abs(O.psnr(out[TF32], clean, peak) - psnr_ref)
     xs32 = out[F.FOE_PREC_FP32].ravel()[np.array(g["sample_index"])]
     err32 = np.abs(xs32 - xs_ref).max() * 255.0 / peak
     errbf = np.abs(out[BF16].ravel()[np.array(g["sample_index"])] - xs_ref).max() * 255.0 / peak
-    print(f"512 {c['name']} peak {peak}: dPSNR(bf16) {dp:.4f} dB; sampled max-abs fp32 {err32:.2e}, bf16 {errbf:.2e}")
-    assert dp <= 0.02
+    print(f"512 {c['name']} peak {peak}: dPSNR(bf16) {dp:.4f} dB, dPSNR(tf32) {dp32:.4f} dB; "
+          f"sampled max-abs fp32 {err32:.2e}, bf16 {errbf:.2e}")
+    assert dp <= 0.02 and dp32 <= 0.02
     assert err32 <= 1e-4
