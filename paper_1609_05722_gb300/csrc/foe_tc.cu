@@ -16,12 +16,17 @@
 //             with warp shuffles (a warp holds one response row of 32 pixels), the vertical part
 //             through shared memory.
 //
-// Roles: warps 0-3 move data between tensor memory and registers (warp w reads TMEM lanes 32w..32w+31,
-// i.e. response row 4t+w of M-tile t) and do the pointwise work; one thread of warp 4 issues the MMAs.
-// R and Z are double-buffered in tensor memory and Psi in shared memory, so the forward MMA of M-tile
-// t+1 and the adjoint MMA of tile t overlap the epilogue of tile t.  Every mbarrier wait is bounded:
-// on expiry the CTA records FOE_ETIMEOUT in *status, drains its MMAs, frees its tensor memory and
-// finishes without further waits.
+// Roles (320 threads): warps 0-7 move data between tensor memory and registers (warps w and w+4 access
+// TMEM lanes 32(w%4)..32(w%4)+31, i.e. response row 4t+w%4 of M-tile t): warps 0-3 run the expert step,
+// warps 4-7 the col2im.  One thread of warp 8 issues the forward MMAs and one thread of warp 9 the
+// adjoint MMAs, so neither kind of MMA waits behind the other's dependencies.
+// Tensor memory holds two response stages (columns 0 and 64) and two adjoint stages Z(t & 1) (columns
+// 128 and 192).  The epilogue writes Psi(t) (packed bf16 pairs, or tf32) over the first columns of R(t)'s
+// stage, and the adjoint MMA reads its A operand from there, so Psi never passes through shared memory;
+// the stage is free again once that MMA is complete, Z(t) once the col2im has loaded it.  Expert and
+// col2im warps run decoupled, so the MMAs of later M-tiles overlap the epilogue of earlier ones.
+// Every mbarrier wait is bounded: on expiry the CTA records FOE_ETIMEOUT in *status, drains its MMAs,
+// frees its tensor memory and finishes without further waits.
 //
 // BF16 range: filters are zero-mean, so K(u - c) = K u for any constant c (the padded image of a
 // constant is constant under symmetric padding; under zero padding the padded zeros are shifted by -c
@@ -41,12 +46,12 @@ constexpr int NMT = RS / 4;            // M-tiles per CTA
 constexpr int EROWS = RS + 7;          // input rows (7 tap rows + 1 zero-weight row)
 constexpr int UR = RS + 7, UC = RS + 8;
 constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quarter
-constexpr int MMA_WARP = NEPI;         // one thread of this warp issues the MMAs
-constexpr int NTHR = 32 * (NEPI + 1);
+constexpr int FWD_WARP = NEPI;         // one thread of this warp issues the forward MMAs
+constexpr int ADJ_WARP = NEPI + 1;     // one thread of this warp issues the adjoint MMAs
+constexpr int NWARP = NEPI + 2;
+constexpr int NTHR = 32 * NWARP;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr int NSTAGE = 4;              // TMEM stages of 64 columns: R (48 columns), then Z over it
-constexpr int NPSI = 3;                // Psi buffers in shared memory
-constexpr int LAG = 2;                 // the adjoint of M-tile g is issued, and its col2im done, 2 M-tiles later
+constexpr uint32_t Z_COL0 = 128;       // R(t) at 64 (t & 1) (48 columns), Z(t) at 128 + 64 (t & 1) (64 columns)
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
@@ -57,30 +62,40 @@ template <bool TF>
 struct TcOps;
 template <>
 struct TcOps<false> {
-    static constexpr int EB = 1, WF = 8 * 48, WA = 6 * 64, PSI = 6 * 128;
+    static constexpr int EB = 1, WF = 8 * 48, WA = 6 * 64;
 };
 template <>
 struct TcOps<true> {
-    static constexpr int EB = 2, WF = 8 * 2 * 48, WA = 12 * 64, PSI = 12 * 128;
+    static constexpr int EB = 2, WF = 8 * 2 * 48, WA = 12 * 64;
 };
+
+// mbarriers
+constexpr int B_FWD = 0;     // [2] forward MMAs of M-tile t complete (t & 1)             count 1 (commit)
+constexpr int B_RFREE = 2;   // [2] adjoint MMAs of M-tile t complete: stage t & 1 free  count 1 (commit)
+constexpr int B_PSI = 4;     // [2] Psi(t) written to tensor memory (t & 1)              count 128
+constexpr int B_ADJ = 6;     // [2] adjoint MMAs of M-tile t complete (t & 1)             count 1 (commit)
+constexpr int B_ZFREE = 8;   // [2] Z(t) loaded by every col2im thread (t & 1)           count 128
+constexpr int B_W = 10;      // filter operand images arrived (bulk copy)                count 1 + tx
+constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
+constexpr int NBAR = 13;
 
 template <bool TF>
 struct TcSmem {
     uint4 E[TcOps<TF>::EB][EROWS * RS];   // forward A operand: entry (row, x) holds u(row, x..x+7)
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
-    uint4 Psi[NPSI][TcOps<TF>::PSI];       // adjoint A operand [buffer][filter chunk][pixel][filters in chunk]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
     float U[UR * UC];           // fp32 input region
     float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
     int srow[UR], scol[UR];     // source row / column of each input-region row / column (-1: zero)
-    uint64_t bar[4 * NSTAGE + 1];
+    uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
-    float red[NTHR / 32];
+    float red[NWARP];
 };
-
-constexpr int B_FWD = 0, B_PSI = NSTAGE, B_ADJ = 2 * NSTAGE, B_ZEMPTY = 3 * NSTAGE, B_DRAIN = 4 * NSTAGE;
+// Wf and Wa are filled by one bulk copy of the packed operand images
+static_assert(offsetof(TcSmem<false>, Wa) == offsetof(TcSmem<false>, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
+static_assert(offsetof(TcSmem<true>, Wa) == offsetof(TcSmem<true>, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -92,6 +107,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -108,7 +128,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Bounded wait for the phase with the given parity; false if the CTA gave up.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
 {
     const long long t0 = clock64();
     for (uint32_t i = 0;; ++i) {
@@ -124,6 +144,13 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_fl
     }
 }
 
+// Fast path: one probe (which may suspend the thread until the phase completes); otherwise the bounded loop.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, abort_flag, status);
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -131,7 +158,9 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     // K-major, no swizzle: core matrices of 8 rows x 16 B; lbo = next core matrix along K,
-    // sbo = next group of 8 rows; bits 46-47 = descriptor version 1.
+    // sbo = next group of 8 rows; bits 46-47 = descriptor version 1.  The start address (bits 0-13,
+    // in 16-byte units) of every operand used here stays below 2^14, so an offset in 16-byte units can
+    // be added to a descriptor directly.
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
@@ -143,30 +172,29 @@ __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
 __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N)
 {
     // D FP32 (bit 4), A TF32 (bits 7-9 = 2), B TF32 (bits 10-12 = 2), both K-major.
     return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+template <bool TF>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum)
-        : "memory");
+    if (TF)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x)
@@ -182,6 +210,17 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 {
     uint32_t r[16];
@@ -195,6 +234,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    tmem_ld16(taddr, v);
+    tmem_ld16(taddr + 16, v + 16);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
@@ -202,15 +247,19 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// bulk global -> shared copy completing on an mbarrier (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
@@ -226,8 +275,87 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Sum of the horizontal partials at (qy, qx) of the response region over the 7 tap rows; rows and
-// columns outside the region are outside the image whenever they are asked for, so they add 0.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                     taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+                 "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *v)
+{
+    tmem_st16(taddr, v);
+    tmem_st16(taddr + 16, v + 16);
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// MMA with the A operand in tensor memory (M = 128 lanes, K packed along columns)
+template <bool TF>
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    if (TF)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+}
+
+// psi = r / (1 + r^2) for a pair of responses with packed f32x2 arithmetic, rounded to a bf16x2 word
+__device__ __forceinline__ uint32_t psi_bf16x2(float r0, float r1)
+{
+    uint64_t a, den, inv, p;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(r0), "f"(r1));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(den) : "l"(a), "l"(0x3f8000003f800000ull));
+    float d0, d1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(den));
+    const float i0 = rcp_approx(d0), i1 = rcp_approx(d1);
+    asm("mov.b64 %0, {%1, %2};" : "=l"(inv) : "f"(i0), "f"(i1));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(a), "l"(inv));
+    float p0, p1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(p0), "=f"(p1) : "l"(p));
+    return pack_bf16x2(p0, p1);
+}
+
+// Sum over the 7 tap rows of the horizontal partials at (qy, qx) of the response region.  Unchecked:
+// for an output position (qy, qx in 3..28) every row qy - a + 3 lies in the region.
+template <bool TF>
+__device__ __forceinline__ float hs_sum(const TcSmem<TF> &S, int qy, int qx)
+{
+    const float *p = &S.Hs[(qy + 3) * RS + qx];
+    float g = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) g += p[a * (RS * RS - RS)];
+    return g;
+}
+
+// The same at an arbitrary region position (padding fold); rows and columns outside the region are
+// outside the image whenever they are asked for, so they add 0.
 template <bool TF>
 __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
 {
@@ -261,67 +389,73 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
     if (S.abort_flag) return;
     __syncthreads();
 
-    // ---- asynchronous staging: group 0 = input region + filter images, group 1 = output-pass operands ----
-    constexpr int NWF = TcOps<TF>::WF, NWA = TcOps<TF>::WA;
-    const uint4 *ops = reinterpret_cast<const uint4 *>(TF ? A.tcops32 : A.tcops);
-    for (int j = tid; j < NWF + NWA; j += NTHR) cp_async16(j < NWF ? &S.Wf[j] : &S.Wa[j - NWF], ops + j);
-    if (tid < UR) S.srow[tid] = pad_index(oy0 - 6 + tid, H, A.bc);
-    else if (tid < 2 * UR) S.scol[tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
-    __syncthreads();
-    for (int j = tid; j < UR * UR; j += NTHR) {
-        const int r = j / UR, c = j % UR;
-        const int sy = S.srow[r], sx = S.scol[c];
-        if (sy < 0 || sx < 0) S.U[r * UC + c] = 0.0f;
-        else cp_async4(&S.U[r * UC + c], uin + (size_t)sy * ld + sx);
-    }
-    cp_async_commit();
-    if (MODE == kStep) {
-        for (int j = tid; j < TO * TO; j += NTHR) {
-            const int gy = oy0 + j / TO, gx = ox0 + j % TO;
-            if (gy >= H || gx >= W) continue;
-            const size_t idx = (size_t)gy * ld + gx;
-            if (D.u_lo) cp_async4(&S.O[0][j], D.u_lo + idx);
-            else S.O[0][j] = 0.0f;
-            cp_async4(&S.O[1][j], D.delta + idx);
-            cp_async4(&S.O[2][j], D.d + idx);
-        }
-    } else {
-        for (int j = tid; j < TO * TO; j += NTHR) {
-            const int gy = oy0 + j / TO, gx = ox0 + j % TO;
-            if (gy < H && gx < W) cp_async4(&S.O[2][j], D.d + (size_t)gy * ld + gx);
-        }
-    }
-    cp_async_commit();
-
+    // ---- barriers, tensor memory, filter operands (one bulk copy) ----
+    constexpr uint32_t WBYTES = sizeof(uint4) * (TcOps<TF>::WF + TcOps<TF>::WA);
     if (tid == 0) {
-        for (int b = 0; b < NSTAGE; ++b) {
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&S.bar[B_FWD + b], 1);
-            mbar_init(&S.bar[B_PSI + b], 32 * NEPI);
+            mbar_init(&S.bar[B_RFREE + b], 1);
+            mbar_init(&S.bar[B_PSI + b], 16 * NEPI);
             mbar_init(&S.bar[B_ADJ + b], 1);
-            mbar_init(&S.bar[B_ZEMPTY + b], 32 * NEPI);
+            mbar_init(&S.bar[B_ZFREE + b], 16 * NEPI);
+            mbar_init(&S.bar[B_DRAIN + b], 1);
         }
-        mbar_init(&S.bar[B_DRAIN], 1);
-        S.abort_flag = 0;
+        mbar_init(&S.bar[B_W], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == MMA_WARP) {
+    if (warp == FWD_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 
+    // ---- asynchronous staging: group 0 = input region, group 1 = output-pass operands ----
+    if (tid < UR) S.srow[tid] = pad_index(oy0 - 6 + tid, H, A.bc);
+    else if (tid < 2 * UR) S.scol[tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
+        bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
+    }
+    for (int r = warp; r < UR; r += NWARP) {
+        const int sy = S.srow[r];
+        const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
+        for (int c = lane; c < UR; c += 32) {
+            const int sx = S.scol[c];
+            if (sy < 0 || sx < 0) S.U[r * UC + c] = 0.0f;
+            else cp_async4(&S.U[r * UC + c], src + sx);
+        }
+    }
+    cp_async_commit();
+    if (lane < TO) {
+        const int gx = ox0 + lane;
+        for (int r = warp; r < TO; r += NWARP) {
+            const int gy = oy0 + r, j = r * TO + lane;
+            if (gy >= H || gx >= W) continue;
+            const size_t idx = (size_t)gy * ld + gx;
+            if (MODE == kStep) {
+                if (D.u_lo) cp_async4(&S.O[0][j], D.u_lo + idx);
+                else S.O[0][j] = 0.0f;
+                cp_async4(&S.O[1][j], D.delta + idx);
+            }
+            cp_async4(&S.O[2][j], D.d + idx);
+        }
+    }
+    cp_async_commit();
+
     // ---- tile mean (BF16 range), then E ----
     cp_async_wait<1>();
     __syncthreads();
     float lsum = 0.0f;
-    for (int j = tid; j < UR * UR; j += NTHR) lsum += S.U[(j / UR) * UC + j % UR];
+    for (int r = warp; r < UR; r += NWARP)
+        for (int c = lane; c < UR; c += 32) lsum += S.U[r * UC + c];
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0) S.red[warp] = lsum;
     __syncthreads();
     float mean = 0.0f;
 #pragma unroll
-    for (int w = 0; w < NTHR / 32; ++w) mean += S.red[w];
+    for (int w = 0; w < NWARP; ++w) mean += S.red[w];
     mean *= 1.0f / (float)(UR * UR);
     for (int j = tid; j < EROWS * RS; j += NTHR) {
         const int i = j / RS, x = j % RS;
@@ -347,62 +481,55 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
     const uint32_t tmem = S.tmem_base;
     volatile int *abort_flag = &S.abort_flag;
 
-    if (warp == MMA_WARP) {
+    if (warp == FWD_WARP || warp == ADJ_WARP) {
         if (lane == 0) {
             // ---------------- MMA issue ----------------
-            constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
-            constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
-            const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
-            const uint32_t wf0 = smem_u32(S.Wf), wa0 = smem_u32(S.Wa);
-            bool ok = true;
-            // stage s = t % NSTAGE holds R(t) (columns 64 s .. 64 s + 47) until the epilogue has read it, then
-            // the adjoint writes Z(t) over it (64 columns); the stage is free again once Z(t) has been read.
-            auto adjoint = [&](int t) {
-                const int s = t % NSTAGE, k = t / NSTAGE;
-                if (!mbar_wait(&S.bar[B_PSI + s], k & 1, abort_flag, status)) return false;
-                fence_after();
-                const uint32_t ps = smem_u32(S.Psi[t % NPSI]);
-                if (TF) {
-                    // K = 48 filters in 6 steps of 8 (two 4-filter chunks each)
+            const int dr = warp == FWD_WARP ? 0 : 1;
+            bool ok = mbar_wait(&S.bar[B_W], 0, abort_flag, status);
+            if (warp == FWD_WARP) {
+                // R(t) = E-window(t) x Wf^T into stage t & 1, once the adjoint of M-tile t - 2 is complete
+                constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
+                const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
+                const uint64_t dE = sdesc(e0, TF ? e1 - e0 : RS * 16, 128), dW = sdesc(smem_u32(S.Wf), 768, 128);
+                for (int t = 0; ok && t < NMT; ++t) {
+                    if (t >= 2 && !mbar_wait(&S.bar[B_RFREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag, status)) break;
+                    fence_after();
+                    const uint32_t d = tmem + 64 * (t & 1);
+                    if (TF) {
+                        // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has
+                        // zero weights and is skipped
 #pragma unroll
-                    for (int kk = 0; kk < 6; ++kk)
-                        mma_tf32(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128),
-                                 sdesc(wa0 + kk * 2 * 1024, 1024, 128), IDA, kk > 0);
-                } else {
+                        for (int kk = 0; kk < 7; ++kk)
+                            mma<TF>(d, dE + (uint64_t)((4 * t + kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
+                    } else {
 #pragma unroll
-                    for (int kk = 0; kk < 3; ++kk)
-                        mma_bf16(tmem + 64 * s, sdesc(ps + kk * 2 * 2048, 2048, 128),
-                                 sdesc(wa0 + kk * 2 * 1024, 1024, 128), IDA, kk > 0);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma<TF>(d, dE + (uint64_t)((4 * t + 2 * kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
+                    }
+                    mma_commit(&S.bar[B_FWD + (t & 1)]);
                 }
-                mma_commit(&S.bar[B_ADJ + s]);
-                return true;
-            };
-            for (int t = 0; t < NMT && ok; ++t) {
-                const int s = t % NSTAGE, k = t / NSTAGE;
-                if (t >= NSTAGE && !mbar_wait(&S.bar[B_ZEMPTY + s], (k - 1) & 1, abort_flag, status)) { ok = false; break; }
-                fence_after();
-                if (TF) {
-                    // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has zero
-                    // weights and is skipped
+            } else {
+                // Z(t) = Psi(t) x Wa^T into Z stage t & 1, once Psi(t) is in tensor memory and Z(t - 2) has
+                // been loaded; A = Psi(t) in the first columns of R(t)'s stage (8 columns per K-step: 16 bf16
+                // or 8 tf32 filters)
+                constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
+                const uint64_t dWa = sdesc(smem_u32(S.Wa), 1024, 128);
+                for (int t = 0; ok && t < NMT; ++t) {
+                    if (!mbar_wait(&S.bar[B_PSI + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                    if (t >= 2 && !mbar_wait(&S.bar[B_ZFREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag, status)) break;
+                    fence_after();
+                    const uint32_t d = tmem + Z_COL0 + 64 * (t & 1), a = tmem + 64 * (t & 1);
 #pragma unroll
-                    for (int kk = 0; kk < 7; ++kk)
-                        mma_tf32(tmem + 64 * s, sdesc(e0 + (4 * t + kk) * RS * 16, e1 - e0, 128),
-                                 sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
-                } else {
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma_bf16(tmem + 64 * s, sdesc(e0 + (4 * t + 2 * kk) * RS * 16, RS * 16, 128),
-                                 sdesc(wf0 + kk * 2 * 768, 768, 128), IDF, kk > 0);
+                    for (int kk = 0; kk < (TF ? 6 : 3); ++kk)
+                        mma_ta<TF>(d, a + 8 * kk, dWa + (uint64_t)(kk * 128), IDA, kk > 0);
+                    mma_commit(&S.bar[B_ADJ + (t & 1)]);
+                    mma_commit(&S.bar[B_RFREE + (t & 1)]);
                 }
-                mma_commit(&S.bar[B_FWD + s]);
-                if (t >= LAG && !adjoint(t - LAG)) ok = false;
             }
-            for (int t = NMT - LAG; ok && t < NMT; ++t)
-                if (!adjoint(t)) ok = false;
-            // all MMAs issued by this thread are complete once the drain barrier flips
-            mma_commit(&S.bar[B_DRAIN]);
+            // all MMAs issued by this thread are complete once its drain barrier flips
+            mma_commit(&S.bar[B_DRAIN + dr]);
             const long long t0 = clock64();
-            while (!mbar_try_wait(&S.bar[B_DRAIN], 0))
+            while (!mbar_try_wait(&S.bar[B_DRAIN + dr], 0))
                 if (clock64() - t0 > kTimeoutCycles) {
                     atomicExch(status, 5);
                     break;
@@ -411,93 +538,89 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
         __syncwarp();
     } else {
         // ---------------- epilogue warps ----------------
-        // warp q = warp % 4 reads TMEM lanes 32q..32q+31 (response row 4t+q of M-tile t); the two warps of a
-        // lane quarter split the filters (half = 0: filters 0-23, 1: 24-47) and the tap rows (0: a 0-3, 1: a 4-6).
-        const int q = warp & 3, half = warp >> 2;
+        // warp w reads and writes TMEM lanes 32q..32q+31, q = w % 4 (response row 4t+q of M-tile t).  Warps 0-3
+        // run the expert step of all 48 filters (R(t) -> Psi(t), in place in R(t)'s stage), warps 4-7 the
+        // col2im of all 7 tap rows (Z(t) -> horizontal partials in shared memory).
+        const int q = warp & 3;
         // interior tile: the whole response region lies in the image, so no response is masked and no
         // lane outside 3..28 is ever read (no padding fold)
         const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + RS - 3 <= H && ox0 + RS - 3 <= W;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        const int m = 32 * q + lane;
-        auto col2im = [&](int t) {
-            const int b = t % NSTAGE, k = t / NSTAGE;
-            if (!mbar_wait(&S.bar[B_ADJ + b], k & 1, abort_flag, status)) return false;
-            fence_after();
-            float z[32];
-            const uint32_t zc = tmem + lane_base + 64 * b + 32 * half;
-            tmem_ld16(zc, z);
-            tmem_ld16(zc + 16, z + 16);
-            tmem_wait_ld();
-            fence_before();
-            mbar_arrive(&S.bar[B_ZEMPTY + b]);
-            const int rr = 4 * t + q;
+        if (warp < 4) {
+            const int gx = ox0 - 3 + lane;
+            for (int t = 0; t < NMT; ++t) {
+                if (!mbar_wait(&S.bar[B_FWD + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                fence_after();
+                const uint32_t rc = tmem + lane_base + 64 * (t & 1);
+                float r[48];
+                tmem_ld32(rc, r);
+                tmem_ld16(rc + 32, r + 32);
+                tmem_wait_ld();
+                const int gy = oy0 - 3 + 4 * t + q;
+                const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
+                if (TF) {
+                    uint32_t w[48];
 #pragma unroll
-            for (int aa = 0; aa < 4; ++aa) {
-                const int a = 4 * half + aa;
-                if (a > 6) break;
-                float h = z[8 * aa + 3];
-                if (interior) {
-#pragma unroll
-                    for (int bb = 0; bb < 3; ++bb) h += __shfl_down_sync(0xffffffffu, z[8 * aa + bb], 3 - bb);
-#pragma unroll
-                    for (int bb = 4; bb < 7; ++bb) h += __shfl_up_sync(0xffffffffu, z[8 * aa + bb], bb - 3);
-                } else {
-#pragma unroll
-                    for (int bb = 0; bb < 7; ++bb) {
-                        if (bb == 3) continue;
-                        const int src = lane + 3 - bb;
-                        const float v = __shfl_sync(0xffffffffu, z[8 * aa + bb], src & 31);
-                        h += (src >= 0 && src < 32) ? v : 0.0f;
+                    for (int j = 0; j < 48; ++j) {
+                        const float r0 = r[j];
+                        w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
                     }
+                    tmem_st32(rc, w);
+                    tmem_st16(rc + 32, w + 32);
+                } else {
+                    uint32_t w[24];
+#pragma unroll
+                    for (int j = 0; j < 24; ++j) w[j] = psi_bf16x2(r[2 * j], r[2 * j + 1]);
+                    if (!interior) {
+#pragma unroll
+                        for (int j = 0; j < 24; ++j) w[j] &= keep;
+                    }
+                    tmem_st16(rc, w);
+                    tmem_st8(rc + 16, w + 16);
                 }
-                S.Hs[(a * RS + rr) * RS + lane] = h;
+                tmem_wait_st();
+                fence_before();
+                mbar_arrive(&S.bar[B_PSI + (t & 1)]);
             }
-            return true;
-        };
-        bool ok = true;
-        for (int t = 0; t < NMT; ++t) {
-            const int b = t % NSTAGE, k = t / NSTAGE;
-            if (!mbar_wait(&S.bar[B_FWD + b], k & 1, abort_flag, status)) { ok = false; break; }
-            fence_after();
-            float r[32];
-            const uint32_t rc = tmem + lane_base + 64 * b + 24 * half;
-            tmem_ld16(rc, r);
-            tmem_ld16(rc + 16, r + 16);  // columns 16-31 of this half; only 16-23 are used
-            tmem_wait_ld();
-            fence_before();
-            const int gy = oy0 - 3 + 4 * t + q, gx = ox0 - 3 + lane;
-            const bool in = interior || (gy >= 0 && gy < H && gx >= 0 && gx < W);
-            if (TF) {
-                uint32_t w[24];
+        } else {
+            for (int t = 0; t < NMT; ++t) {
+                if (!mbar_wait(&S.bar[B_ADJ + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                fence_after();
+                float z[56];
+                const uint32_t zc = tmem + lane_base + Z_COL0 + 64 * (t & 1);
+                tmem_ld32(zc, z);
+                tmem_ld16(zc + 32, z + 32);
+                tmem_ld8(zc + 48, z + 48);  // tap row 7 has zero weights
+                tmem_wait_ld();
+                fence_before();
+                mbar_arrive(&S.bar[B_ZFREE + (t & 1)]);
+                const int rr = 4 * t + q;
 #pragma unroll
-                for (int j = 0; j < 24; ++j) {
-                    const float r0 = r[j];
-                    w[j] = in ? to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) : 0u;
+                for (int a = 0; a < 7; ++a) {
+                    const float *za = z + 8 * a;
+                    float h;
+                    if (interior) {
+                        const float s0 = __shfl_down_sync(0xffffffffu, za[0], 3);
+                        const float s1 = __shfl_down_sync(0xffffffffu, za[1], 2);
+                        const float s2 = __shfl_down_sync(0xffffffffu, za[2], 1);
+                        const float s4 = __shfl_up_sync(0xffffffffu, za[4], 1);
+                        const float s5 = __shfl_up_sync(0xffffffffu, za[5], 2);
+                        const float s6 = __shfl_up_sync(0xffffffffu, za[6], 3);
+                        h = ((za[3] + s0) + (s1 + s2)) + ((s4 + s5) + s6);
+                    } else {
+                        h = za[3];
+#pragma unroll
+                        for (int bb = 0; bb < 7; ++bb) {
+                            if (bb == 3) continue;
+                            const int src = lane + 3 - bb;
+                            const float v = __shfl_sync(0xffffffffu, za[bb], src & 31);
+                            h += (src >= 0 && src < 32) ? v : 0.0f;
+                        }
+                    }
+                    S.Hs[(a * RS + rr) * RS + lane] = h;
                 }
-                uint4 *dst = &S.Psi[t % NPSI][(6 * half) * 128 + m];
-#pragma unroll
-                for (int kc = 0; kc < 6; ++kc)
-                    dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
-            } else {
-                uint32_t w[12];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) {
-                    const float r0 = r[2 * j], r1 = r[2 * j + 1];
-                    const float p0 = r0 * rcp_approx(fmaf(r0, r0, 1.0f));
-                    const float p1 = r1 * rcp_approx(fmaf(r1, r1, 1.0f));
-                    w[j] = in ? pack_bf16x2(p0, p1) : 0u;
-                }
-                uint4 *dst = &S.Psi[t % NPSI][(3 * half) * 128 + m];
-#pragma unroll
-                for (int kc = 0; kc < 3; ++kc)
-                    dst[kc * 128] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
             }
-            fence_async_smem();
-            mbar_arrive(&S.bar[B_PSI + b]);  // R(t) has been read and Psi(t) written: the adjoint may overwrite the stage
-            if (t >= LAG && !col2im(t - LAG)) { ok = false; break; }
         }
-        for (int t = NMT - LAG; ok && t < NMT; ++t)
-            if (!col2im(t)) ok = false;
     }
 
     cp_async_wait<0>();
@@ -506,47 +629,57 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
 
     // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
     const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TO > H - 3 || ox0 + TO > W - 3);
-    for (int j = tid; j < TO * TO; j += NTHR) {
-        const int yo = 3 + j / TO, xo = 3 + j % TO;
-        const int gy = oy0 + yo - 3, gx = ox0 + xo - 3;
-        if (gy >= H || gx >= W) continue;
-        float g = hs_gather(S, yo, xo);
-        if (ring) {
-            const int my = gy < 3 ? -1 - gy : (gy >= H - 3 ? 2 * H - 1 - gy : -1000);
-            const int mx = gx < 3 ? -1 - gx : (gx >= W - 3 ? 2 * W - 1 - gx : -1000);
-            if (my != -1000) g += hs_gather(S, my - oy0 + 3, xo);
-            if (mx != -1000) g += hs_gather(S, yo, mx - ox0 + 3);
-            if (my != -1000 && mx != -1000) g += hs_gather(S, my - oy0 + 3, mx - ox0 + 3);
-        }
-        const size_t idx = (size_t)gy * ld + gx;
-        const float uh = S.U[(yo + 3) * UC + xo + 3];
-        if (MODE == kGrad) {
-            D.out[idx] = g + data_grad(uh, S.O[2][j], D.model, D.sc.lambda);
-        } else {
-            float nh, nl, nd;
-            ipiano_update(g, uh, S.O[0][j], S.O[1][j], S.O[2][j], D.model, D.sc, nh, nl, nd);
-            D.u_hi[A.parity ^ 1][idx] = nh;
-            if (D.u_lo) D.u_lo[idx] = nl;
-            D.delta[idx] = nd;
+    if (lane < TO) {
+        const int xo = 3 + lane, gx = ox0 + lane;
+        for (int r = warp; r < TO; r += NWARP) {
+            const int yo = 3 + r, gy = oy0 + r, j = r * TO + lane;
+            if (gy >= H || gx >= W) continue;
+            float g = hs_sum(S, yo, xo);
+            if (ring) {
+                const int my = gy < 3 ? -1 - gy : (gy >= H - 3 ? 2 * H - 1 - gy : -1000);
+                const int mx = gx < 3 ? -1 - gx : (gx >= W - 3 ? 2 * W - 1 - gx : -1000);
+                if (my != -1000) g += hs_gather(S, my - oy0 + 3, xo);
+                if (mx != -1000) g += hs_gather(S, yo, mx - ox0 + 3);
+                if (my != -1000 && mx != -1000) g += hs_gather(S, my - oy0 + 3, mx - ox0 + 3);
+            }
+            const size_t idx = (size_t)gy * ld + gx;
+            const float uh = S.U[(yo + 3) * UC + xo + 3];
+            if (MODE == kGrad) {
+                D.out[idx] = g + data_grad(uh, S.O[2][j], D.model, D.sc.lambda);
+            } else {
+                float nh, nl, nd;
+                ipiano_update(g, uh, S.O[0][j], S.O[1][j], S.O[2][j], D.model, D.sc, nh, nl, nd);
+                D.u_hi[A.parity ^ 1][idx] = nh;
+                if (D.u_lo) D.u_lo[idx] = nl;
+                D.delta[idx] = nd;
+            }
         }
     }
 
-    if (warp == MMA_WARP) {
+    if (warp == FWD_WARP) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
+}
+
+// Dynamic shared memory per CTA.  At most two CTAs share an SM (2 x 256 TMEM columns); the request is
+// raised so that a third CTA, which would wait in tcgen05.alloc, is never made resident.
+template <bool TF>
+constexpr size_t smem_request()
+{
+    return sizeof(TcSmem<TF>) > 80 * 1024 ? sizeof(TcSmem<TF>) : 80 * 1024;
 }
 
 }  // namespace
 
 int tc_tile_h() { return TO; }
 int tc_tile_w() { return TO; }
-size_t tc_smem_bytes() { return sizeof(TcSmem<false>); }
+size_t tc_smem_bytes() { return smem_request<false>(); }
 
 cudaError_t tc_setup()
 {
     cudaError_t e;
-    const int b16 = (int)sizeof(TcSmem<false>), t32 = (int)sizeof(TcSmem<true>);
+    const int b16 = (int)smem_request<false>(), t32 = (int)smem_request<true>();
     if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
     if ((e = cudaFuncSetAttribute(k_foe_tc<kGrad, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
     if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32))) return e;
@@ -559,11 +692,11 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     if (tiles <= 0) return cudaSuccess;
     if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
     if (tf32) {
-        if (mode == kStep) k_foe_tc<kStep, true><<<tiles, NTHR, sizeof(TcSmem<true>), s>>>(a, d_status);
-        else k_foe_tc<kGrad, true><<<tiles, NTHR, sizeof(TcSmem<true>), s>>>(a, d_status);
+        if (mode == kStep) k_foe_tc<kStep, true><<<tiles, NTHR, smem_request<true>(), s>>>(a, d_status);
+        else k_foe_tc<kGrad, true><<<tiles, NTHR, smem_request<true>(), s>>>(a, d_status);
     } else {
-        if (mode == kStep) k_foe_tc<kStep, false><<<tiles, NTHR, sizeof(TcSmem<false>), s>>>(a, d_status);
-        else k_foe_tc<kGrad, false><<<tiles, NTHR, sizeof(TcSmem<false>), s>>>(a, d_status);
+        if (mode == kStep) k_foe_tc<kStep, false><<<tiles, NTHR, smem_request<false>(), s>>>(a, d_status);
+        else k_foe_tc<kGrad, false><<<tiles, NTHR, smem_request<false>(), s>>>(a, d_status);
     }
     return cudaGetLastError();
 }
