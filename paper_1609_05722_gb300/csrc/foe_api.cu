@@ -19,12 +19,12 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
         base += 5 * plane;
         models[j] = resolve_model(o->model, d.peak);
         FOE_CUDA(c, foe::launch_init(d.y, d.H, d.W, d.ld, d.ld, models[j], o->zero_c, slots[j].d, slots[j].uh0,
-                                     slots[j].ul, slots[j].delta, s));
+                                     lo_plane(o->prec, slots[j].ul), slots[j].delta, s));
         const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
         ImgDesc e{};
         e.u_hi[0] = slots[j].uh0;
         e.u_hi[1] = slots[j].uh1;
-        e.u_lo = slots[j].ul;
+        e.u_lo = lo_plane(o->prec, slots[j].ul);
         e.delta = slots[j].delta;
         e.d = slots[j].d;
         e.H = d.H;
@@ -56,7 +56,7 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
     for (int j = 0; j < n; ++j) {
         const foe_image_desc &d = descs[order[j]];
         const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0;
-        FOE_CUDA(c, foe::launch_output(uf, slots[j].ul, d.H, d.W, d.ld, d.ld, models[j], d.x, s));
+        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, slots[j].ul), d.H, d.W, d.ld, d.ld, models[j], d.x, s));
     }
     return FOE_OK;
 }
@@ -187,12 +187,12 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     const size_t plane = (size_t)H * ld;
     if ((st = ensure_ws(c, 5 * plane * sizeof(float))) != FOE_OK) return st;
     Slot sl = carve((float *)c->ws, plane);
-    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, sl.ul, sl.delta, s));
+    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, lo_plane(o->prec, sl.ul), sl.delta, s));
     args_begin(c, o->bc);
     ImgDesc d{};
     d.u_hi[0] = sl.uh0;
     d.u_hi[1] = sl.uh1;
-    d.u_lo = sl.ul;
+    d.u_lo = lo_plane(o->prec, sl.ul);
     d.delta = sl.delta;
     d.d = sl.d;
     d.out = nullptr;
@@ -210,7 +210,7 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     }
     if ((st = prof_end(c, s, ev, o->iters, (double)H * W * o->iters)) != FOE_OK) return st;
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
-    FOE_CUDA(c, foe::launch_output(uf, sl.ul, H, W, ld, ld, model, x, s));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, s));
     if (rep) {
         int dev_status = 0;
         FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -492,12 +492,12 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
     // every plane that the solve reads is written first by k_init (d, u_hi[0], u_lo, delta) or by the
     // step that precedes the read (u_hi[1]), so the previous call's contents need no clearing
     Slot sl = carve(ws, (size_t)H * ld);
-    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, sl.ul, sl.delta, s));
+    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, lo_plane(o->prec, sl.ul), sl.delta, s));
     args_begin(c, o->bc);
     ImgDesc d{};
     d.u_hi[0] = sl.uh0;
     d.u_hi[1] = sl.uh1;
-    d.u_lo = sl.ul;
+    d.u_lo = lo_plane(o->prec, sl.ul);
     d.delta = sl.delta;
     d.d = sl.d;
     d.H = H;
@@ -511,6 +511,6 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
         if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
     }
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
-    FOE_CUDA(c, foe::launch_output(uf, sl.ul, H, W, ld, ld, model, x, s));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, s));
     return FOE_OK;
 }

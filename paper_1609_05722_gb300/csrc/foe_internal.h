@@ -323,6 +323,10 @@ inline void prof_clear(foe_ctx *c)
     c->prof_pixel_iters = 0.0;
 }
 
+// The FP32 path keeps the iterate as an unevaluated pair u_hi + u_lo; the tensor-core paths (whose BF16 / TF32
+// operand rounding dominates the error) keep a plain FP32 u_hi, so their u_lo plane is left out everywhere.
+inline float *lo_plane(int prec, float *ul) { return prec == FOE_PREC_FP32 ? ul : nullptr; }
+
 // Per-image workspace: u_hi[2], u_lo, delta, d, each H x ld floats.
 struct Slot {
     float *uh0, *uh1, *ul, *delta, *d;

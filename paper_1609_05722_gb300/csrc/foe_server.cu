@@ -122,7 +122,7 @@ foe_status enqueue_iterations(foe_server *sv)
             ImgDesc d{};
             d.u_hi[0] = odd ? sl.uh1 : sl.uh0;  // this request's own parity: read buffer first
             d.u_hi[1] = odd ? sl.uh0 : sl.uh1;
-            d.u_lo = sl.ul;
+            d.u_lo = lo_plane(o.prec, sl.ul);
             d.delta = sl.delta;
             d.d = sl.d;
             d.H = r->H;
@@ -244,7 +244,7 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
         const Slot sl = request_slot(sv, r);
         FOE_CUDA(c, cudaMemcpy2DAsync(sl.d, r->ld * sizeof(float), r->y_host, r->y_pitch * sizeof(float),
                                       r->W * sizeof(float), r->H, cudaMemcpyHostToDevice, sv->stream));
-        FOE_CUDA(c, foe::launch_init(sl.d, r->H, r->W, r->ld, r->ld, r->model, o.zero_c, sl.d, sl.uh0, sl.ul, sl.delta,
+        FOE_CUDA(c, foe::launch_init(sl.d, r->H, r->W, r->ld, r->ld, r->model, o.zero_c, sl.d, sl.uh0, lo_plane(o.prec, sl.ul), sl.delta,
                                      sv->stream));
     }
     // 2. iterations of every admitted request
@@ -290,7 +290,7 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
         }
         const Slot sl = request_slot(sv, r);
         const float *uf = (r->iters & 1) ? sl.uh1 : sl.uh0;
-        FOE_CUDA(c, foe::launch_output(uf, sl.ul, r->H, r->W, r->ld, r->ld, r->model, sl.delta, sv->stream));
+        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o.prec, sl.ul), r->H, r->W, r->ld, r->ld, r->model, sl.delta, sv->stream));
         FOE_CUDA(c, cudaMemcpy2DAsync(r->x_host, r->x_pitch * sizeof(float), sl.delta, r->ld * sizeof(float),
                                       r->W * sizeof(float), r->H, cudaMemcpyDeviceToHost, sv->stream));
         finished.push_back(r);

@@ -31,6 +31,7 @@
 // BF16 range: filters are zero-mean, so K(u - c) = K u for any constant c (the padded image of a
 // constant is constant under symmetric padding; under zero padding the padded zeros are shifted by -c
 // too).  The tile mean is subtracted before rounding u to BF16.
+#include <algorithm>
 #include <cstdint>
 
 #include "foe_common.cuh"
@@ -85,9 +86,10 @@ struct TcSmem {
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
-    float U[UR * UC];           // fp32 input region
-    float O[3][TO * TO];        // output-pass operands, prefetched: u_lo, delta, d
-    int srow[UR], scol[UR];     // source row / column of each input-region row / column (-1: zero)
+    float U[2][UR * UC];        // fp32 input region (this tile / the next one, prefetched)
+    float O[2][3][TO * TO];     // output-pass operands [unused], delta, d (this tile / the next one)
+    int srow[2][UR], scol[2][UR];  // source row / column of each input-region row / column (-1: zero)
+    int geo[2][3];              // image, oy0, ox0 of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -178,23 +180,62 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// Bounded wait with a warp-uniform result (every lane waits; the warp gives up if any lane gave up).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
+{
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag, status));
+}
+
+// Warp-uniform issue: the whole warp executes these, one elected lane (the lowest, lane 0) issues.
 template <bool TF>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+__device__ __forceinline__ void mma_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
 {
     if (TF)
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(a), "l"(b), "r"(idesc), "r"(accum)
             : "memory");
     else
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(a), "l"(b), "r"(idesc), "r"(accum)
             : "memory");
+}
+
+template <bool TF>
+__device__ __forceinline__ void mma_ta_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    if (TF)
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+}
+
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x)
@@ -202,12 +243,6 @@ __device__ __forceinline__ uint32_t to_tf32(float x)
     uint32_t d;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(d) : "f"(x));
     return d;
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
@@ -282,13 +317,6 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
-                 "r"(v[2]), "r"(v[3])
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -306,26 +334,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *v)
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// MMA with the A operand in tensor memory (M = 128 lanes, K packed along columns)
-template <bool TF>
-__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if (TF)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-}
-
 // psi = r / (1 + r^2) for a pair of responses with packed f32x2 arithmetic, rounded to a bf16x2 word
 __device__ __forceinline__ uint32_t psi_bf16x2(float r0, float r1)
 {
@@ -340,6 +348,33 @@ __device__ __forceinline__ uint32_t psi_bf16x2(float r0, float r1)
     float p0, p1;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(p0), "=f"(p1) : "l"(p));
     return pack_bf16x2(p0, p1);
+}
+
+// iPiano step (Eq. iPianoupdate) with the proximal map of the data term, on a plain FP32 iterate: the tensor-core
+// paths round u and psi to BF16 / TF32, which dominates the error, so the compensated (hi + lo) state of the FP32
+// path is not kept here (u_lo is neither read nor written).  The I-divergence prox (t + sqrt(t^2 + 4cd)) / 2,
+// t = u~ - c, is evaluated as 2cd / (sqrt(t^2 + 4cd) - t) for t < 0, which avoids the cancellation.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void ipiano_update_f32(float g, float uh, float delta, float d, int model,
+                                                  const StepConsts &sc, float &nh, float &ndelta)
+{
+    const float ut = uh + fmaf(sc.gamma, delta, -sc.tau * g);
+    float p;
+    if (model == kAnsL2) {
+        p = fmaf(sc.a1_hi, ut, sc.a2_hi * d);
+    } else {
+        const float c = sc.c_hi, t = ut - c, cd4 = 4.0f * c * d;
+        const float sq = sqrt_approx(fmaf(t, t, cd4));
+        p = t >= 0.0f ? 0.5f * (t + sq) : __fdividef(0.5f * cd4, sq - t);
+    }
+    nh = p;
+    ndelta = p - uh;
 }
 
 // Sum over the 7 tap rows of the horizontal partials at (qy, qx) of the response region.  Unchecked:
@@ -369,19 +404,64 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
     return g;
 }
 
+// Image and origin of a tile.
+__device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0)
+{
+    im = tile_image(A, tile);
+    const ImgDesc &D = A.img[im];
+    const int lt = tile - A.tile_prefix[im];
+    oy0 = (lt / D.tiles_x) * TO;
+    ox0 = (lt % D.tiles_x) * TO;
+}
+
+// Issue the asynchronous copies of a tile's input region and output-pass operands into buffer b (all threads;
+// one cp.async group).  Positions outside the padded image are zero-filled with plain stores.
+template <int MODE, bool TF>
+__device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
+                                           int lane)
+{
+    if (tid == 0) tile_geometry(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2]);
+    __syncthreads();
+    const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
+    const ImgDesc &D = A.img[im];
+    const int H = D.H, W = D.W, ld = D.ld;
+    if (tid < UR) S.srow[b][tid] = pad_index(oy0 - 6 + tid, H, A.bc);
+    else if (tid < 2 * UR) S.scol[b][tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
+    __syncthreads();
+    const float *uin = D.u_hi[A.parity];
+    float *U = S.U[b];
+    for (int r = warp; r < UR; r += NWARP) {
+        const int sy = S.srow[b][r];
+        const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
+        for (int c = lane; c < UR; c += 32) {
+            const int sx = S.scol[b][c];
+            if (sy < 0 || sx < 0) U[r * UC + c] = 0.0f;
+            else cp_async4(&U[r * UC + c], src + sx);
+        }
+    }
+    if (lane < TO) {
+        const int gx = ox0 + lane;
+        for (int r = warp; r < TO; r += NWARP) {
+            const int gy = oy0 + r, j = r * TO + lane;
+            if (gy >= H || gx >= W) continue;
+            const size_t idx = (size_t)gy * ld + gx;
+            if (MODE == kStep) cp_async4(&S.O[b][1][j], D.delta + idx);
+            cp_async4(&S.O[b][2][j], D.d + idx);
+        }
+    }
+    cp_async_commit();
+}
+
+// Persistent: CTA c processes tiles c, c + gridDim.x, ...; tensor memory, barriers and the filter operands
+// are set up once, and the input region of the next tile is copied in while the current one is computed.
 template <int MODE, bool TF>
 __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem<TF> &S = *reinterpret_cast<TcSmem<TF> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
-    const int im = tile_image(A, tile);
-    const ImgDesc &D = A.img[im];
-    const int lt = tile - A.tile_prefix[im];
-    const int oy0 = (lt / D.tiles_x) * TO, ox0 = (lt % D.tiles_x) * TO;
-    const int H = D.H, W = D.W, ld = D.ld;
-    const float *uin = D.u_hi[A.parity];
+    const int ntiles = A.tile_prefix[A.nimg];
+    if ((int)blockIdx.x >= ntiles) return;
 
     // an earlier launch that gave up leaves *status set: then do nothing (CTA-uniform decision)
     if (tid == 0) S.abort_flag = *(volatile int *)status;
@@ -409,253 +489,274 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-
-    // ---- asynchronous staging: group 0 = input region, group 1 = output-pass operands ----
-    if (tid < UR) S.srow[tid] = pad_index(oy0 - 6 + tid, H, A.bc);
-    else if (tid < 2 * UR) S.scol[tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
     __syncthreads();
     if (tid == 0) {
         mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
         bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
     }
-    for (int r = warp; r < UR; r += NWARP) {
-        const int sy = S.srow[r];
-        const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
-        for (int c = lane; c < UR; c += 32) {
-            const int sx = S.scol[c];
-            if (sy < 0 || sx < 0) S.U[r * UC + c] = 0.0f;
-            else cp_async4(&S.U[r * UC + c], src + sx);
-        }
-    }
-    cp_async_commit();
-    if (lane < TO) {
-        const int gx = ox0 + lane;
-        for (int r = warp; r < TO; r += NWARP) {
-            const int gy = oy0 + r, j = r * TO + lane;
-            if (gy >= H || gx >= W) continue;
-            const size_t idx = (size_t)gy * ld + gx;
-            if (MODE == kStep) {
-                if (D.u_lo) cp_async4(&S.O[0][j], D.u_lo + idx);
-                else S.O[0][j] = 0.0f;
-                cp_async4(&S.O[1][j], D.delta + idx);
-            }
-            cp_async4(&S.O[2][j], D.d + idx);
-        }
-    }
-    cp_async_commit();
-
-    // ---- tile mean (BF16 range), then E ----
-    cp_async_wait<1>();
-    __syncthreads();
-    float lsum = 0.0f;
-    for (int r = warp; r < UR; r += NWARP)
-        for (int c = lane; c < UR; c += 32) lsum += S.U[r * UC + c];
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0) S.red[warp] = lsum;
-    __syncthreads();
-    float mean = 0.0f;
-#pragma unroll
-    for (int w = 0; w < NWARP; ++w) mean += S.red[w];
-    mean *= 1.0f / (float)(UR * UR);
-    for (int j = tid; j < EROWS * RS; j += NTHR) {
-        const int i = j / RS, x = j % RS;
-        const float *src = &S.U[i * UC + x];
-        if (TF) {
-            S.E[0][j] = make_uint4(to_tf32(src[0] - mean), to_tf32(src[1] - mean), to_tf32(src[2] - mean),
-                                   to_tf32(src[3] - mean));
-            S.E[TcOps<TF>::EB - 1][j] = make_uint4(to_tf32(src[4] - mean), to_tf32(src[5] - mean),
-                                                   to_tf32(src[6] - mean), to_tf32(src[7] - mean));
-        } else {
-            uint4 e;
-            e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
-            e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
-            e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
-            e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
-            S.E[0][j] = e;
-        }
-    }
-    fence_async_smem();
+    stage_tile<MODE, TF>(A, S, blockIdx.x, 0, tid, warp, lane);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_base;
     volatile int *abort_flag = &S.abort_flag;
 
-    if (warp == FWD_WARP || warp == ADJ_WARP) {
-        if (lane == 0) {
-            // ---------------- MMA issue ----------------
-            const int dr = warp == FWD_WARP ? 0 : 1;
-            bool ok = mbar_wait(&S.bar[B_W], 0, abort_flag, status);
-            if (warp == FWD_WARP) {
-                // R(t) = E-window(t) x Wf^T into stage t & 1, once the adjoint of M-tile t - 2 is complete
-                constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
-                const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
-                const uint64_t dE = sdesc(e0, TF ? e1 - e0 : RS * 16, 128), dW = sdesc(smem_u32(S.Wf), 768, 128);
-                for (int t = 0; ok && t < NMT; ++t) {
-                    if (t >= 2 && !mbar_wait(&S.bar[B_RFREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag, status)) break;
-                    fence_after();
-                    const uint32_t d = tmem + 64 * (t & 1);
-                    if (TF) {
-                        // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has
-                        // zero weights and is skipped
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2];
+        const ImgDesc &D = A.img[im];
+        const int H = D.H, W = D.W, ld = D.ld;
+
+        // this tile's copies (issued one tile earlier) have landed; start the next tile's
+        cp_async_wait<0>();
+        __syncthreads();
+        if (tile + (int)gridDim.x < ntiles) stage_tile<MODE, TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+
+        // ---- tile mean (BF16 range), then E ----
+        const float *Ub = S.U[buf];
+        float lsum = 0.0f;
+        for (int r = warp; r < UR; r += NWARP)
+            for (int c = lane; c < UR; c += 32) lsum += Ub[r * UC + c];
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) S.red[warp] = lsum;
+        __syncthreads();
+        float mean = 0.0f;
 #pragma unroll
-                        for (int kk = 0; kk < 7; ++kk)
-                            mma<TF>(d, dE + (uint64_t)((4 * t + kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
-                    } else {
+        for (int w = 0; w < NWARP; ++w) mean += S.red[w];
+        mean *= 1.0f / (float)(UR * UR);
+        for (int j = tid; j < EROWS * RS; j += NTHR) {
+            const int i = j / RS, x = j % RS;
+            const float *src = &Ub[i * UC + x];
+            if (TF) {
+                S.E[0][j] = make_uint4(to_tf32(src[0] - mean), to_tf32(src[1] - mean), to_tf32(src[2] - mean),
+                                       to_tf32(src[3] - mean));
+                S.E[TcOps<TF>::EB - 1][j] = make_uint4(to_tf32(src[4] - mean), to_tf32(src[5] - mean),
+                                                       to_tf32(src[6] - mean), to_tf32(src[7] - mean));
+            } else {
+                uint4 e;
+                e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
+                e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
+                e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
+                e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
+                S.E[0][j] = e;
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+
+        if (warp == FWD_WARP || warp == ADJ_WARP) {
+            {
+                // ---------------- MMA issue (warp-uniform; one elected lane issues) ----------------
+                // stage barriers complete four times per tile, so their phase parities repeat every tile; the waits
+                // for M-tile t - 2 reach back into the previous tile for t < 2 (g counts M-tiles over all tiles)
+                bool ok = k > 0 || mbar_wait_warp(&S.bar[B_W], 0, abort_flag, status);
+                if (warp == FWD_WARP) {
+                    // R(t) = E-window(t) x Wf^T into stage t & 1, once the adjoint of M-tile t - 2 is complete
+                    constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
+                    const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
+                    const uint64_t dE = sdesc(e0, TF ? e1 - e0 : RS * 16, 128), dW = sdesc(smem_u32(S.Wf), 768, 128);
+                    for (int t = 0; ok && t < NMT; ++t) {
+                        const int g = NMT * k + t;
+                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_RFREE + (t & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
+                        fence_after();
+                        const uint32_t d = tmem + 64 * (t & 1);
+                        if (TF) {
+                            // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has
+                            // zero weights and is skipped
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma<TF>(d, dE + (uint64_t)((4 * t + 2 * kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
+                            for (int kk = 0; kk < 7; ++kk)
+                                mma_elect<TF>(d, dE + (uint64_t)((4 * t + kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
+                        } else {
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_elect<TF>(d, dE + (uint64_t)((4 * t + 2 * kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
+                        }
+                        commit_elect(&S.bar[B_FWD + (t & 1)]);
                     }
-                    mma_commit(&S.bar[B_FWD + (t & 1)]);
+                } else {
+                    // Z(t) = Psi(t) x Wa^T into Z stage t & 1, once Psi(t) is in tensor memory and Z(t - 2) has
+                    // been loaded; A = Psi(t) in the first columns of R(t)'s stage (8 columns per K-step: 16 bf16
+                    // or 8 tf32 filters)
+                    constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
+                    const uint64_t dWa = sdesc(smem_u32(S.Wa), 1024, 128);
+                    for (int t = 0; ok && t < NMT; ++t) {
+                        if (!mbar_wait_warp(&S.bar[B_PSI + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                        const int g = NMT * k + t;
+                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_ZFREE + (t & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
+                        fence_after();
+                        const uint32_t d = tmem + Z_COL0 + 64 * (t & 1), a = tmem + 64 * (t & 1);
+#pragma unroll
+                        for (int kk = 0; kk < (TF ? 6 : 3); ++kk)
+                            mma_ta_elect<TF>(d, a + 8 * kk, dWa + (uint64_t)(kk * 128), IDA, kk > 0);
+                        commit_elect(&S.bar[B_ADJ + (t & 1)]);
+                        commit_elect(&S.bar[B_RFREE + (t & 1)]);
+                    }
+                }
+            }
+            __syncwarp();
+        } else {
+            // ---------------- epilogue warps ----------------
+            // warp w reads and writes TMEM lanes 32q..32q+31, q = w % 4 (response row 4t+q of M-tile t).  Warps 0-3
+            // run the expert step of all 48 filters (R(t) -> Psi(t), in place in R(t)'s stage), warps 4-7 the
+            // col2im of all 7 tap rows (Z(t) -> horizontal partials in shared memory).
+            const int q = warp & 3;
+            // interior tile: the whole response region lies in the image, so no response is masked and no
+            // lane outside 3..28 is ever read (no padding fold)
+            const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + RS - 3 <= H && ox0 + RS - 3 <= W;
+            const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+            if (warp < 4) {
+                const int gx = ox0 - 3 + lane;
+                for (int t = 0; t < NMT; ++t) {
+                    if (!mbar_wait(&S.bar[B_FWD + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                    fence_after();
+                    const uint32_t rc = tmem + lane_base + 64 * (t & 1);
+                    float r[48];
+                    tmem_ld32(rc, r);
+                    tmem_ld16(rc + 32, r + 32);
+                    tmem_wait_ld();
+                    const int gy = oy0 - 3 + 4 * t + q;
+                    const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
+                    if (TF) {
+                        uint32_t w[48];
+#pragma unroll
+                        for (int j = 0; j < 48; ++j) {
+                            const float r0 = r[j];
+                            w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
+                        }
+                        tmem_st32(rc, w);
+                        tmem_st16(rc + 32, w + 32);
+                    } else {
+                        uint32_t w[24];
+#pragma unroll
+                        for (int j = 0; j < 24; ++j) w[j] = psi_bf16x2(r[2 * j], r[2 * j + 1]);
+                        if (!interior) {
+#pragma unroll
+                            for (int j = 0; j < 24; ++j) w[j] &= keep;
+                        }
+                        tmem_st16(rc, w);
+                        tmem_st8(rc + 16, w + 16);
+                    }
+                    tmem_wait_st();
+                    fence_before();
+                    mbar_arrive(&S.bar[B_PSI + (t & 1)]);
                 }
             } else {
-                // Z(t) = Psi(t) x Wa^T into Z stage t & 1, once Psi(t) is in tensor memory and Z(t - 2) has
-                // been loaded; A = Psi(t) in the first columns of R(t)'s stage (8 columns per K-step: 16 bf16
-                // or 8 tf32 filters)
-                constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
-                const uint64_t dWa = sdesc(smem_u32(S.Wa), 1024, 128);
-                for (int t = 0; ok && t < NMT; ++t) {
-                    if (!mbar_wait(&S.bar[B_PSI + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
-                    if (t >= 2 && !mbar_wait(&S.bar[B_ZFREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag, status)) break;
+                for (int t = 0; t < NMT; ++t) {
+                    if (!mbar_wait(&S.bar[B_ADJ + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
                     fence_after();
-                    const uint32_t d = tmem + Z_COL0 + 64 * (t & 1), a = tmem + 64 * (t & 1);
-#pragma unroll
-                    for (int kk = 0; kk < (TF ? 6 : 3); ++kk)
-                        mma_ta<TF>(d, a + 8 * kk, dWa + (uint64_t)(kk * 128), IDA, kk > 0);
-                    mma_commit(&S.bar[B_ADJ + (t & 1)]);
-                    mma_commit(&S.bar[B_RFREE + (t & 1)]);
-                }
-            }
-            // all MMAs issued by this thread are complete once its drain barrier flips
-            mma_commit(&S.bar[B_DRAIN + dr]);
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&S.bar[B_DRAIN + dr], 0))
-                if (clock64() - t0 > kTimeoutCycles) {
-                    atomicExch(status, 5);
-                    break;
-                }
-        }
-        __syncwarp();
-    } else {
-        // ---------------- epilogue warps ----------------
-        // warp w reads and writes TMEM lanes 32q..32q+31, q = w % 4 (response row 4t+q of M-tile t).  Warps 0-3
-        // run the expert step of all 48 filters (R(t) -> Psi(t), in place in R(t)'s stage), warps 4-7 the
-        // col2im of all 7 tap rows (Z(t) -> horizontal partials in shared memory).
-        const int q = warp & 3;
-        // interior tile: the whole response region lies in the image, so no response is masked and no
-        // lane outside 3..28 is ever read (no padding fold)
-        const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + RS - 3 <= H && ox0 + RS - 3 <= W;
-        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        if (warp < 4) {
-            const int gx = ox0 - 3 + lane;
-            for (int t = 0; t < NMT; ++t) {
-                if (!mbar_wait(&S.bar[B_FWD + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
-                fence_after();
-                const uint32_t rc = tmem + lane_base + 64 * (t & 1);
-                float r[48];
-                tmem_ld32(rc, r);
-                tmem_ld16(rc + 32, r + 32);
-                tmem_wait_ld();
-                const int gy = oy0 - 3 + 4 * t + q;
-                const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
-                if (TF) {
-                    uint32_t w[48];
-#pragma unroll
-                    for (int j = 0; j < 48; ++j) {
-                        const float r0 = r[j];
-                        w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
-                    }
-                    tmem_st32(rc, w);
-                    tmem_st16(rc + 32, w + 32);
-                } else {
-                    uint32_t w[24];
-#pragma unroll
-                    for (int j = 0; j < 24; ++j) w[j] = psi_bf16x2(r[2 * j], r[2 * j + 1]);
-                    if (!interior) {
-#pragma unroll
-                        for (int j = 0; j < 24; ++j) w[j] &= keep;
-                    }
-                    tmem_st16(rc, w);
-                    tmem_st8(rc + 16, w + 16);
-                }
-                tmem_wait_st();
-                fence_before();
-                mbar_arrive(&S.bar[B_PSI + (t & 1)]);
-            }
-        } else {
-            for (int t = 0; t < NMT; ++t) {
-                if (!mbar_wait(&S.bar[B_ADJ + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
-                fence_after();
-                float z[56];
-                const uint32_t zc = tmem + lane_base + Z_COL0 + 64 * (t & 1);
-                tmem_ld32(zc, z);
-                tmem_ld16(zc + 32, z + 32);
-                tmem_ld8(zc + 48, z + 48);  // tap row 7 has zero weights
-                tmem_wait_ld();
-                fence_before();
-                mbar_arrive(&S.bar[B_ZFREE + (t & 1)]);
-                const int rr = 4 * t + q;
-#pragma unroll
-                for (int a = 0; a < 7; ++a) {
-                    const float *za = z + 8 * a;
-                    float h;
+                    float z[56];
+                    const uint32_t zc = tmem + lane_base + Z_COL0 + 64 * (t & 1);
+                    tmem_ld32(zc, z);
+                    tmem_ld16(zc + 32, z + 32);
+                    tmem_ld8(zc + 48, z + 48);  // tap row 7 has zero weights
+                    tmem_wait_ld();
+                    fence_before();
+                    mbar_arrive(&S.bar[B_ZFREE + (t & 1)]);
+                    const int rr = 4 * t + q;
                     if (interior) {
-                        const float s0 = __shfl_down_sync(0xffffffffu, za[0], 3);
-                        const float s1 = __shfl_down_sync(0xffffffffu, za[1], 2);
-                        const float s2 = __shfl_down_sync(0xffffffffu, za[2], 1);
-                        const float s4 = __shfl_up_sync(0xffffffffu, za[4], 1);
-                        const float s5 = __shfl_up_sync(0xffffffffu, za[5], 2);
-                        const float s6 = __shfl_up_sync(0xffffffffu, za[6], 3);
-                        h = ((za[3] + s0) + (s1 + s2)) + ((s4 + s5) + s6);
-                    } else {
-                        h = za[3];
+                        // all 42 shuffles first, then the sums: independent work to cover the shuffle latency
+                        float sh[7][6];
 #pragma unroll
-                        for (int bb = 0; bb < 7; ++bb) {
-                            if (bb == 3) continue;
-                            const int src = lane + 3 - bb;
-                            const float v = __shfl_sync(0xffffffffu, za[bb], src & 31);
-                            h += (src >= 0 && src < 32) ? v : 0.0f;
+                        for (int a = 0; a < 7; ++a) {
+                            sh[a][0] = __shfl_down_sync(0xffffffffu, z[8 * a + 0], 3);
+                            sh[a][1] = __shfl_down_sync(0xffffffffu, z[8 * a + 1], 2);
+                            sh[a][2] = __shfl_down_sync(0xffffffffu, z[8 * a + 2], 1);
+                            sh[a][3] = __shfl_up_sync(0xffffffffu, z[8 * a + 4], 1);
+                            sh[a][4] = __shfl_up_sync(0xffffffffu, z[8 * a + 5], 2);
+                            sh[a][5] = __shfl_up_sync(0xffffffffu, z[8 * a + 6], 3);
+                        }
+#pragma unroll
+                        for (int a = 0; a < 7; ++a)
+                            S.Hs[(a * RS + rr) * RS + lane] =
+                                ((z[8 * a + 3] + sh[a][0]) + (sh[a][1] + sh[a][2])) + ((sh[a][3] + sh[a][4]) + sh[a][5]);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) {
+                            const float *za = z + 8 * a;
+                            float h;
+                            h = za[3];
+#pragma unroll
+                            for (int bb = 0; bb < 7; ++bb) {
+                                if (bb == 3) continue;
+                                const int src = lane + 3 - bb;
+                                const float v = __shfl_sync(0xffffffffu, za[bb], src & 31);
+                                h += (src >= 0 && src < 32) ? v : 0.0f;
+                            }
+                            S.Hs[(a * RS + rr) * RS + lane] = h;
                         }
                     }
-                    S.Hs[(a * RS + rr) * RS + lane] = h;
                 }
             }
         }
+
+        fence_before();
+        __syncthreads();
+
+        // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
+        // warp w handles output rows w, w + 9/10, w + 2*(9/10) (lane = column): the rows are unrolled so that their
+        // independent update chains interleave
+        const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TO > H - 3 || ox0 + TO > W - 3);
+        constexpr int NR = (TO + NWARP - 1) / NWARP;
+        if (lane < TO) {
+            const int xo = 3 + lane, gx = ox0 + lane;
+            float g[NR], uh[NR];
+            bool ok_r[NR];
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                const int r = warp + k2 * NWARP, yo = 3 + r, gy = oy0 + r;
+                ok_r[k2] = r < TO && gy < H && gx < W;
+                g[k2] = 0.0f;
+                uh[k2] = 0.0f;
+                if (ok_r[k2]) {
+                    g[k2] = hs_sum(S, yo, xo);
+                    uh[k2] = Ub[(yo + 3) * UC + xo + 3];
+                    if (ring) {
+                        const int my = gy < 3 ? -1 - gy : (gy >= H - 3 ? 2 * H - 1 - gy : -1000);
+                        const int mx = gx < 3 ? -1 - gx : (gx >= W - 3 ? 2 * W - 1 - gx : -1000);
+                        if (my != -1000) g[k2] += hs_gather(S, my - oy0 + 3, xo);
+                        if (mx != -1000) g[k2] += hs_gather(S, yo, mx - ox0 + 3);
+                        if (my != -1000 && mx != -1000) g[k2] += hs_gather(S, my - oy0 + 3, mx - ox0 + 3);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                if (!ok_r[k2]) continue;
+                const int r = warp + k2 * NWARP, j = r * TO + lane;
+                const size_t idx = (size_t)(oy0 + r) * ld + gx;
+                if (MODE == kGrad) {
+                    D.out[idx] = g[k2] + data_grad(uh[k2], S.O[buf][2][j], D.model, D.sc.lambda);
+                } else {
+                    float nh, nd;
+                    ipiano_update_f32(g[k2], uh[k2], S.O[buf][1][j], S.O[buf][2][j], D.model, D.sc, nh, nd);
+                    D.u_hi[A.parity ^ 1][idx] = nh;
+                    D.delta[idx] = nd;
+                }
+            }
+        }
+
+        // Hs and this tile's buffers are reused by the next tiles
+        __syncthreads();
+        if (*abort_flag) break;
     }
 
+    // every MMA issued by the two MMA threads is complete before tensor memory is released
+    if (warp == FWD_WARP || warp == ADJ_WARP) {
+        uint64_t *bar = &S.bar[B_DRAIN + (warp == FWD_WARP ? 0 : 1)];
+        commit_elect(bar);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(bar, 0))
+            if (clock64() - t0 > kTimeoutCycles) {
+                atomicExch(status, 5);
+                break;
+            }
+    }
     cp_async_wait<0>();
     fence_before();
     __syncthreads();
-
-    // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
-    const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TO > H - 3 || ox0 + TO > W - 3);
-    if (lane < TO) {
-        const int xo = 3 + lane, gx = ox0 + lane;
-        for (int r = warp; r < TO; r += NWARP) {
-            const int yo = 3 + r, gy = oy0 + r, j = r * TO + lane;
-            if (gy >= H || gx >= W) continue;
-            float g = hs_sum(S, yo, xo);
-            if (ring) {
-                const int my = gy < 3 ? -1 - gy : (gy >= H - 3 ? 2 * H - 1 - gy : -1000);
-                const int mx = gx < 3 ? -1 - gx : (gx >= W - 3 ? 2 * W - 1 - gx : -1000);
-                if (my != -1000) g += hs_gather(S, my - oy0 + 3, xo);
-                if (mx != -1000) g += hs_gather(S, yo, mx - ox0 + 3);
-                if (my != -1000 && mx != -1000) g += hs_gather(S, my - oy0 + 3, mx - ox0 + 3);
-            }
-            const size_t idx = (size_t)gy * ld + gx;
-            const float uh = S.U[(yo + 3) * UC + xo + 3];
-            if (MODE == kGrad) {
-                D.out[idx] = g + data_grad(uh, S.O[2][j], D.model, D.sc.lambda);
-            } else {
-                float nh, nl, nd;
-                ipiano_update(g, uh, S.O[0][j], S.O[1][j], S.O[2][j], D.model, D.sc, nh, nl, nd);
-                D.u_hi[A.parity ^ 1][idx] = nh;
-                if (D.u_lo) D.u_lo[idx] = nl;
-                D.delta[idx] = nd;
-            }
-        }
-    }
-
     if (warp == FWD_WARP) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -691,12 +792,18 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     const int tiles = a.tile_prefix[a.nimg];
     if (tiles <= 0) return cudaSuccess;
     if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // persistent CTAs: as many as are resident at once (tensor memory admits two per SM, one for TF32)
+    const int grid = std::min(tiles, (tf32 ? 1 : 2) * sms);
     if (tf32) {
-        if (mode == kStep) k_foe_tc<kStep, true><<<tiles, NTHR, smem_request<true>(), s>>>(a, d_status);
-        else k_foe_tc<kGrad, true><<<tiles, NTHR, smem_request<true>(), s>>>(a, d_status);
+        if (mode == kStep) k_foe_tc<kStep, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
+        else k_foe_tc<kGrad, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
     } else {
-        if (mode == kStep) k_foe_tc<kStep, false><<<tiles, NTHR, smem_request<false>(), s>>>(a, d_status);
-        else k_foe_tc<kGrad, false><<<tiles, NTHR, smem_request<false>(), s>>>(a, d_status);
+        if (mode == kStep) k_foe_tc<kStep, false><<<grid, NTHR, smem_request<false>(), s>>>(a, d_status);
+        else k_foe_tc<kGrad, false><<<grid, NTHR, smem_request<false>(), s>>>(a, d_status);
     }
     return cudaGetLastError();
 }
