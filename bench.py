@@ -307,7 +307,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--no-train", dest="train", action="store_false",
@@ -400,15 +400,15 @@ def main():
             dist.barrier()
         return total, loop_ms, launches, pix
 
-    prec_main = F.FOE_PREC_BF16 if args.prec == "bf16" else F.FOE_PREC_FP32
+    prec_main = {"bf16": F.FOE_PREC_BF16, "tf32": F.FOE_PREC_TF32, "fp32": F.FOE_PREC_FP32}[args.prec]
     try:
         F.foe_denoise_batch(ctx, descs(xs, ys, 0, 1, 1), F.SolveOpts(prec=prec_main), stream=stream)
     except F.FoeError as e:
-        if e.status == F.FOE_EUNSUPPORTED and prec_main == F.FOE_PREC_BF16:
+        if e.status == F.FOE_EUNSUPPORTED and prec_main != F.FOE_PREC_FP32:
             prec_main = F.FOE_PREC_FP32  # tensor-core path not built into this library
         else:
             raise
-    dtype = "bf16" if prec_main == F.FOE_PREC_BF16 else "f32"
+    dtype = {F.FOE_PREC_BF16: "bf16", F.FOE_PREC_TF32: "tf32", F.FOE_PREC_FP32: "f32"}[prec_main]
 
     sampler = ClockSampler(local if world > 1 else 0)
     sampler.start()
@@ -422,8 +422,10 @@ def main():
     peaks, peak_src = measured_peaks()
     avg_launch_s = (loop_ms / 1e3) / max(launches, 1)
     pix_per_launch = pix / max(launches, 1)
-    if prec_main == F.FOE_PREC_BF16:
+    if prec_main != F.FOE_PREC_FP32:
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        if prec_main == F.FOE_PREC_TF32:
+            peak *= 1.1 / 2.25  # nominal dense TF32 : BF16 rate
         bound, unit, key = "tensor", "TFLOP/s", "foe_tc_step"
     else:
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -431,7 +433,8 @@ def main():
     achieved = pix_per_launch * FLOP_PER_PIXEL_ITER / avg_launch_s / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": ncu_traffic(key), "peak_source": f"{peak_src}"
-                + (" bf16_tflops_sustained" if bound == "tensor" else " 152 SMs x 128 FFMA/clk x 2 x sm_max_mhz"),
+                + ((" bf16_tflops_sustained" + (" x 1.1/2.25 (nominal tf32:bf16)" if dtype == "tf32" else ""))
+                   if bound == "tensor" else " 152 SMs x 128 FFMA/clk x 2 x sm_max_mhz"),
                 "kernel": key, "avg_launch_us": avg_launch_s * 1e6, "pixels_per_launch": pix_per_launch}
 
     # plain FP32 path on the same workload (the comparison the metric names)
