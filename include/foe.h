@@ -83,7 +83,9 @@ typedef struct {
     float tau;            /* step size; 0 = the context's default for (bc, gamma) */
     float tol;            /* reserved (0): iterations always run to `iters` */
     int iters;            /* >= 0 */
-    foe_step_mode step;   /* FOE_STEP_FIXED only */
+    foe_step_mode step;   /* FIXED: constant tau.  BACKTRACK (foe_denoise with FOE_PREC_FP32 only; the other
+                             entry points return FOE_EUNSUPPORTED): Lipschitz backtracking on the prior, see
+                             foe_denoise */
     foe_bc bc;
     foe_precision prec;
     float zero_c;         /* direct model: zero counts are replaced by zero_c (Sec. 3.1.1), >= 0 */
@@ -97,8 +99,10 @@ typedef struct {
 typedef struct {
     int iters_done;
     int model_used;       /* resolved foe_model (never AUTO) */
-    float tau_used;
+    float tau_used;       /* FIXED: the step size; BACKTRACK: the last accepted one */
     foe_status status;
+    int backtracks;       /* BACKTRACK: rejected trials (0 for FIXED) */
+    double lipschitz_final; /* BACKTRACK: L after the last step; FIXED: the L that tau_used corresponds to */
 } foe_report;
 
 /* One image of a batch (foe_denoise_batch). */
@@ -133,11 +137,25 @@ FOE_API foe_status foe_step_size(const foe_ctx *ctx, foe_bc bc, float gamma, flo
 /* Host-only, needs no device: the Lipschitz bound L above for a prior that has no context yet. */
 FOE_API foe_status foe_prior_lipschitz(const foe_prior *prior, foe_bc bc, double *lipschitz_out);
 
+/* Trials of the context's last FOE_STEP_BACKTRACK solve, in order: tau[i] the trial's step size,
+ * accepted[i] 1 if it was taken, 0 if it was rejected (L doubled).  Copies min(n, max_n) entries into the host
+ * arrays (which may be NULL when max_n = 0) and returns n, the number of trials; -1 on invalid arguments.
+ * Accepted trials are exactly one per iteration. */
+FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted, int max_n);
+
 /* Denoises one image (steps a1-a10 of the solve): data term from y, iPiano iterations, output map.
  *   y    device, noisy counts (non-negative integers stored as FP32), H x W, pitch ld
  *   x    device, output in the intensity domain, H x W, pitch ld (may alias y)
  *   peak the noise level (max of the clean image, Sec. 2.1); only FOE_MODEL_AUTO reads it
- *   rep  host, nullable; if given, the stream is synchronised and the report filled */
+ *   rep  host, nullable; if given, the stream is synchronised and the report filled
+ * opts.step = FOE_STEP_BACKTRACK (FP32 only; step a9): the step size of iPiano (Sec. 2.3, given there only as a
+ * symbol) is found per iteration by Lipschitz backtracking on the smooth part F = E_FoE: a trial with estimate
+ * L uses tau = 2 (1 - gamma) / (L + 2e-3) and is accepted when
+ *   F(u+) <= F(u) + <grad F(u), u+ - u> + L/2 ||u+ - u||^2    (FP64 reductions on the GPU),
+ * otherwise L doubles and the step is retried from the same u; after each accepted step L is divided by 1.5.
+ * L starts at the bound of foe_step_size (or at the L implied by opts.tau when it is > 0).  The host reads
+ * three scalars per trial (one synchronisation each), so this mode is for accuracy, not throughput.
+ * foe_step_log returns the trials of the last such solve. */
 FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *opts, void *stream, foe_report *rep);
 

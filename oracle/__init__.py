@@ -221,11 +221,48 @@ class Problem:
         e = lib().orc_energy_grad(C.byref(self.p), _p(u), _p(d), _p(g))
         return e, g
 
-    def step(self, d, u, u_prev):
+    def step(self, d, u, u_prev, tau=None):
+        """One iPiano step (Sec. 2.3, Eq. iPianoupdate); tau, if given, replaces the problem's step size for
+        this step only (the replay of a step-size sequence)."""
         d, u, up = _d(d), _d(u), _d(u_prev)
         un = np.empty_like(u)
-        lib().orc_ipiano_step(C.byref(self.p), _p(d), _p(u), _p(up), _p(un))
+        p = self.p
+        if tau is not None:
+            p = Params()
+            C.memmove(C.byref(p), C.byref(self.p), C.sizeof(Params))
+            p.tau = float(tau)
+        lib().orc_ipiano_step(C.byref(p), _p(d), _p(u), _p(up), _p(un))
         return un
+
+    def ipiano_backtrack(self, d, u0, iters, L0, c2=1e-3):
+        """iPiano with Lipschitz backtracking on the smooth part F = E_FoE (Sec. 2.3 gives tau and gamma only as
+        symbols; this is the backtracking rule of the iPiano method): a trial with estimate L takes
+        tau = 2 (1 - gamma) / (L + 2 c2) and is accepted when
+            F(u+) <= F(u) + <grad F(u), u+ - u> + L/2 ||u+ - u||^2,
+        else L doubles and the trial is repeated from the same u; after an accepted step L is divided by 1.5.
+        Returns (u, u_prev, trials) with trials a list of (tau, accepted, L)."""
+        gamma = self.p.gamma
+        k, a, bc = self.k, self.alpha, self.p.bc
+        u = _d(u0).copy()
+        up = u.copy()
+        F = prior_energy(k, a, u, bc)
+        L = float(L0)
+        trials = []
+        for _ in range(iters):
+            g = prior_grad(k, a, u, bc)
+            while True:
+                tau = 2.0 * (1.0 - gamma) / (L + 2.0 * c2)
+                un = self.step(d, u, up, tau=tau)
+                du = un - u
+                Fn = prior_energy(k, a, un, bc)
+                ok = Fn <= F + float(np.sum(g * du)) + 0.5 * L * float(np.sum(du * du))
+                trials.append((tau, ok, L))
+                if ok:
+                    break
+                L *= 2.0
+            up, u, F = u, un, Fn
+            L /= 1.5
+        return u, up, trials
 
     def ipiano(self, d, u0, u_prev0, iters, trace=False):
         d = _d(d)

@@ -169,6 +169,126 @@ foe_status foe_step_size(const foe_ctx *ctx, foe_bc bc, float gamma, float *tau_
     return FOE_OK;
 }
 
+// iPiano (Sec. 2.3, Eq. iPianoupdate) with Lipschitz backtracking on the smooth part F = E_FoE (the prior; the
+// data term is the proximal part).  A trial with constant L uses tau = 2 (1 - gamma) / (L + 2 c2), c2 = 1e-3, and is
+// accepted when F(u+) <= F(u) + <grad F(u), u+ - u> + L / 2 ||u+ - u||^2 (FP64 reductions on the GPU, decided on
+// the host); otherwise L doubles and the trial is repeated from the same u.  After an accepted step L is divided
+// by 1.5.  L starts at the context's certified bound (or at the L implied by opts->tau when it is set).  Every
+// trial is one fused FP32 step launch, so rejected trials restore u_lo and delta from a snapshot.
+static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H, int W, int ld, int model,
+                                    const foe_solve_opts *o, cudaStream_t s, foe_report *rep)
+{
+    if (o->prec != FOE_PREC_FP32) {
+        set_err(c, "FOE_STEP_BACKTRACK needs FOE_PREC_FP32");
+        return FOE_EUNSUPPORTED;
+    }
+    foe_status st;
+    const size_t plane = (size_t)H * ld;
+    if ((st = ensure_ws(c, 8 * plane * sizeof(float))) != FOE_OK) return st;
+    Slot sl = carve((float *)c->ws, plane);
+    float *gpl = (float *)c->ws + 5 * plane, *snap_lo = gpl + plane, *snap_dl = snap_lo + plane;
+    const double c2 = 1e-3, gam = o->gamma;
+    int tiles = 0;
+    // launch arguments for one image: read u0 (parity 0), write u1; prior_only for the gradient / energy
+    auto set_args = [&](float *u0, float *u1, float tau, int prior_only) {
+        args_begin(c, o->bc);
+        ImgDesc d{};
+        d.u_hi[0] = u0;
+        d.u_hi[1] = u1;
+        d.u_lo = sl.ul;
+        d.delta = sl.delta;
+        d.d = sl.d;
+        d.out = gpl;
+        d.H = H;
+        d.W = W;
+        d.ld = ld;
+        d.model = model;
+        d.sc = step_consts(tau, o->gamma, o->lambda);
+        args_add(c, FOE_PREC_FP32, d);
+        c->args.prior_only = prior_only;
+        tiles = c->args.tile_prefix[1];
+    };
+    set_args(sl.uh0, nullptr, 0.0f, 1);
+    const int nb = foe::dot2_blocks(H);
+    if ((st = ensure_partials(c, tiles + 2 * nb + 4)) != FOE_OK) return st;
+    double *dot_part = c->d_partials + tiles, *outs = dot_part + 2 * nb;  // outs: <g, du>, |du|^2, F(u+)
+    auto prior_energy = [&](float *u, double *dst) -> foe_status {
+        set_args(u, nullptr, 0.0f, 1);
+        c->args.partials = c->d_partials;
+        foe_status e = launch(c, FOE_PREC_FP32, foe::kEnergy, s);
+        if (e != FOE_OK) return e;
+        FOE_CUDA(c, foe::launch_reduce(c->d_partials, tiles, dst, s));
+        return FOE_OK;
+    };
+
+    FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, sl.ul, sl.delta, s));
+    double L = o->tau > 0.0f ? 2.0 * (1.0 - gam) / (double)o->tau - 2.0 * c2 : 2.0 * kappa(o->bc) * c->symbol_max;
+    if (!(L > 0.0)) {
+        set_err(c, "opts->tau implies a non-positive Lipschitz estimate");
+        return FOE_EINVAL;
+    }
+    c->bt_tau.clear();
+    c->bt_accepted.clear();
+    double h[3], Fn = 0.0;
+    if ((st = prior_energy(sl.uh0, outs + 2)) != FOE_OK) return st;
+    FOE_CUDA(c, cudaMemcpyAsync(&Fn, outs + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FOE_CUDA(c, cudaStreamSynchronize(s));
+    float *cur = sl.uh0, *nxt = sl.uh1;
+    int backtracks = 0;
+    float tau = 0.0f;
+    for (int n = 0; n < o->iters; ++n) {
+        set_args(cur, nullptr, 0.0f, 1);
+        if ((st = launch(c, FOE_PREC_FP32, foe::kGrad, s)) != FOE_OK) return st;  // g = grad F(u^n)
+        FOE_CUDA(c, cudaMemcpyAsync(snap_lo, sl.ul, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        FOE_CUDA(c, cudaMemcpyAsync(snap_dl, sl.delta, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        for (int trial = 0;; ++trial) {
+            if (trial > 0) {
+                FOE_CUDA(c, cudaMemcpyAsync(sl.ul, snap_lo, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                FOE_CUDA(c, cudaMemcpyAsync(sl.delta, snap_dl, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            }
+            tau = (float)(2.0 * (1.0 - gam) / (L + 2.0 * c2));
+            set_args(cur, nxt, tau, 0);
+            if ((st = launch(c, FOE_PREC_FP32, foe::kStep, s)) != FOE_OK) return st;  // u+ (delta = u+ - u^n)
+            FOE_CUDA(c, foe::launch_dot2(gpl, sl.delta, H, W, ld, dot_part, outs, s));
+            if ((st = prior_energy(nxt, outs + 2)) != FOE_OK) return st;
+            FOE_CUDA(c, cudaMemcpyAsync(h, outs, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            FOE_CUDA(c, cudaStreamSynchronize(s));
+            if (!std::isfinite(h[0]) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
+                set_err(c, "non-finite energy or step at iteration %d", n);
+                return FOE_ENONFINITE;
+            }
+            const bool accept = h[2] <= Fn + h[0] + 0.5 * L * h[1];
+            c->bt_tau.push_back(tau);
+            c->bt_accepted.push_back(accept ? 1 : 0);
+            if (accept) {
+                Fn = h[2];
+                break;
+            }
+            L *= 2.0;
+            ++backtracks;
+            if (trial >= 60) {
+                set_err(c, "backtracking did not find an accepted step at iteration %d", n);
+                return FOE_ENONFINITE;
+            }
+        }
+        std::swap(cur, nxt);
+        L /= 1.5;
+    }
+    FOE_CUDA(c, foe::launch_output(cur, sl.ul, H, W, ld, ld, model, x, s));
+    if (rep) {
+        int dev_status = 0;
+        FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FOE_CUDA(c, cudaStreamSynchronize(s));
+        rep->iters_done = o->iters;
+        rep->model_used = model;
+        rep->tau_used = tau;
+        rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
+        rep->backtracks = backtracks;
+        rep->lipschitz_final = L;
+    }
+    return FOE_OK;
+}
+
 foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *o, void *stream, foe_report *rep)
 {
@@ -183,6 +303,7 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int model = resolve_model(o->model, peak);
+    if (o->step == FOE_STEP_BACKTRACK) return denoise_backtrack(c, y, x, H, W, ld, model, o, s, rep);
     const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
     const size_t plane = (size_t)H * ld;
     if ((st = ensure_ws(c, 5 * plane * sizeof(float))) != FOE_OK) return st;
@@ -219,6 +340,8 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
         rep->model_used = model;
         rep->tau_used = tau;
         rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
+        rep->backtracks = 0;
+        rep->lipschitz_final = 2.0 * (1.0 - (double)o->gamma) / (double)tau - 2e-3;
         if (dev_status) {
             FOE_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
             set_err(c, "a device-side wait expired during the solve");
@@ -232,7 +355,7 @@ foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, con
 {
     if (!c) return FOE_EINVAL;
     foe_status st;
-    if ((st = check_opts(c, o)) != FOE_OK) return st;
+    if ((st = check_opts_fixed(c, o, "foe_denoise_batch")) != FOE_OK) return st;
     if (!descs || n < 1 || n > foe::kMaxBatch) {
         set_err(c, "batch size must be in 1..%d", foe::kMaxBatch);
         return FOE_EINVAL;
@@ -472,7 +595,7 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
 {
     if (!c) return FOE_EINVAL;
     foe_status st;
-    if ((st = check_opts(c, o)) != FOE_OK) return st;
+    if ((st = check_opts_fixed(c, o, "foe_denoise_static")) != FOE_OK) return st;
     if ((st = check_image(c, y, H, W, ld, "y")) != FOE_OK) return st;
     if ((st = check_image(c, x, H, W, ld, "x")) != FOE_OK) return st;
     if ((size_t)H * (size_t)ld > kStaticMaxPlane) {
@@ -513,4 +636,16 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
     FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, s));
     return FOE_OK;
+}
+
+
+extern "C" int foe_step_log(const foe_ctx *c, float *tau, unsigned char *accepted, int max_n)
+{
+    if (!c || max_n < 0 || (max_n > 0 && (!tau || !accepted))) return -1;
+    const int n = (int)c->bt_tau.size();
+    for (int i = 0; i < n && i < max_n; ++i) {
+        tau[i] = c->bt_tau[i];
+        accepted[i] = c->bt_accepted[i];
+    }
+    return n;
 }

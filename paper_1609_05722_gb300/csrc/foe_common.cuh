@@ -46,6 +46,7 @@ struct LaunchArgs {
     int parity;
     int bc;
     int nchunks;               // ceil(nf / 8)
+    int prior_only;            // kGrad / kEnergy: the FoE prior term alone (no data term), 0 otherwise
     const float *wts;          // device [48][49], correlation form w_i(a, b) = k_i(-a, -b)
     const float *alpha;        // device [48]
     double *partials;          // kEnergy: one FP64 partial per tile

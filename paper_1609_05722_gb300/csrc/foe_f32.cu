@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
             const int gx = tx0 + ox0 + p;
             if (gy < H && gx < W) {
                 const size_t idx = (size_t)gy * ld + gx;
-                eacc += data_energy(S.u[(oy + R0) * UCOLS + ox0 + p + C0], D.d[idx], D.model, D.sc.lambda);
+                if (!A.prior_only)
+                    eacc += data_energy(S.u[(oy + R0) * UCOLS + ox0 + p + C0], D.d[idx], D.model, D.sc.lambda);
             }
         }
         for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
         const float g = h[p] + hr[p];
         const float uh = S.u[(oy + R0) * UCOLS + ox0 + p + C0];
         if (MODE == kGrad) {
-            D.out[idx] = g + data_grad(uh, D.d[idx], D.model, D.sc.lambda);
+            D.out[idx] = A.prior_only ? g : g + data_grad(uh, D.d[idx], D.model, D.sc.lambda);
         } else {
             const float ul = D.u_lo ? D.u_lo[idx] : 0.0f;
             float nh, nl, nd;

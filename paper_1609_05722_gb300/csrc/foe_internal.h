@@ -39,6 +39,9 @@ struct foe_ctx {
     cudaGraphExec_t batch_exec = nullptr;   // cached graph of the last captured foe_denoise_batch
     long prof_launches = 0;
     double prof_pixel_iters = 0.0;
+    // trial log of the last FOE_STEP_BACKTRACK solve (foe_step_log)
+    std::vector<float> bt_tau;
+    std::vector<unsigned char> bt_accepted;
     char err[512] = {};
 };
 
@@ -183,13 +186,25 @@ inline foe_status check_opts(foe_ctx *c, const foe_solve_opts *o)
     if (!(o->gamma >= 0.0f && o->gamma < 1.0f)) { set_err(c, "gamma must be in [0, 1)"); return FOE_EINVAL; }
     if (!(o->tau >= 0.0f) || !std::isfinite(o->tau)) { set_err(c, "tau must be >= 0"); return FOE_EINVAL; }
     if (o->iters < 0) { set_err(c, "iters must be >= 0"); return FOE_EINVAL; }
-    if (o->step != FOE_STEP_FIXED) { set_err(c, "only FOE_STEP_FIXED is implemented"); return FOE_EUNSUPPORTED; }
+    if (o->step != FOE_STEP_FIXED && o->step != FOE_STEP_BACKTRACK) { set_err(c, "bad step mode"); return FOE_EINVAL; }
     if (o->bc != FOE_BC_SYMMETRIC && o->bc != FOE_BC_ZERO) { set_err(c, "bad bc"); return FOE_EINVAL; }
     if (o->prec != FOE_PREC_FP32 && o->prec != FOE_PREC_BF16 && o->prec != FOE_PREC_TF32) {
         set_err(c, "bad precision");
         return FOE_EINVAL;
     }
     if (!(o->zero_c >= 0.0f) || !std::isfinite(o->zero_c)) { set_err(c, "zero_c must be >= 0"); return FOE_EINVAL; }
+    return FOE_OK;
+}
+
+// Entry points other than foe_denoise run fixed steps only.
+inline foe_status check_opts_fixed(foe_ctx *c, const foe_solve_opts *o, const char *entry)
+{
+    const foe_status st = check_opts(c, o);
+    if (st != FOE_OK) return st;
+    if (o->step != FOE_STEP_FIXED) {
+        set_err(c, "%s: FOE_STEP_BACKTRACK is implemented in foe_denoise only", entry);
+        return FOE_EUNSUPPORTED;
+    }
     return FOE_OK;
 }
 
@@ -238,6 +253,7 @@ inline void args_begin(foe_ctx *c, int bc)
     A.parity = 0;
     A.bc = bc;
     A.nchunks = (c->nf + 7) / 8;
+    A.prior_only = 0;
     A.wts = c->d_wts;
     A.alpha = c->d_alpha;
     A.partials = c->d_partials;

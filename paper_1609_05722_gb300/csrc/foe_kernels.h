@@ -40,4 +40,10 @@ cudaError_t launch_anscombe(const float *y, float *v, long n, cudaStream_t s);
 cudaError_t launch_inverse(const float *z, float *x, long n, cudaStream_t s);
 cudaError_t launch_reduce(const double *p, int n, double *out, cudaStream_t s);
 
+// Step control (foe_backtrack.cu): out[0] = sum g * dl, out[1] = sum dl * dl over an H x W plane (pitch ld),
+// FP64, in a fixed order (per-block partials in `partials`, 2 * dot2_blocks(H) doubles, then one block).
+int dot2_blocks(int H);
+cudaError_t launch_dot2(const float *g, const float *dl, int H, int W, int ld, double *partials, double *out,
+                        cudaStream_t s);
+
 }  // namespace foe

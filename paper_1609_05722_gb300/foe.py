@@ -37,7 +37,8 @@ class foe_solve_opts(C.Structure):
 
 
 class foe_report(C.Structure):
-    _fields_ = [("iters_done", C.c_int), ("model_used", C.c_int), ("tau_used", C.c_float), ("status", C.c_int)]
+    _fields_ = [("iters_done", C.c_int), ("model_used", C.c_int), ("tau_used", C.c_float), ("status", C.c_int),
+                ("backtracks", C.c_int), ("lipschitz_final", C.c_double)]
 
 
 class foe_image_desc(C.Structure):
@@ -79,6 +80,7 @@ def lib() -> C.CDLL:
             "foe_destroy": (None, [vp]),
             "foe_step_size": (i, [vp, i, f, C.POINTER(f), C.POINTER(d)]),
             "foe_prior_lipschitz": (i, [C.POINTER(foe_prior), i, C.POINTER(d)]),
+            "foe_step_log": (i, [vp, C.POINTER(f), C.POINTER(C.c_ubyte), i]),
             "foe_denoise": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
             "foe_denoise_batch": (i, [vp, C.POINTER(foe_image_desc), i, C.POINTER(foe_solve_opts), vp]),
             "foe_energy_grad": (i, [vp, vp, vp, i, i, i, i, f, i, i, C.POINTER(d), vp, vp]),
@@ -212,8 +214,21 @@ def foe_denoise(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts
                              C.byref(rep) if report else None), ctx, "foe_denoise")
     if report:
         return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
-                "status": rep.status}
+                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final}
     return None
+
+
+def foe_step_log(ctx):
+    """Trials of the last FOE_STEP_BACKTRACK solve: (tau per trial, accepted flag per trial) as numpy arrays."""
+    import numpy as np
+    n = lib().foe_step_log(ctx, None, None, 0)
+    if n < 0:
+        raise FoeError(FOE_EINVAL, "foe_step_log: invalid arguments")
+    tau = np.zeros(n, dtype=np.float32)
+    acc = np.zeros(n, dtype=np.uint8)
+    if n:
+        lib().foe_step_log(ctx, tau.ctypes.data_as(C.POINTER(C.c_float)), acc.ctypes.data_as(C.POINTER(C.c_ubyte)), n)
+    return tau, acc.astype(bool)
 
 
 def foe_denoise_static(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts | None = None,

@@ -380,3 +380,63 @@ def test_training_gradient_matches_central_differences(bank, bc):
         an = float((dk * dkd).sum() + (da * dad).sum())
         assert an == pytest.approx(fd, rel=1e-4, abs=1e-9)
         assert an == pytest.approx(rich, rel=1e-6, abs=1e-10)
+
+
+# ------------------------------------------------- step control: Lipschitz backtracking (step a9)
+
+def test_descent_lemma_at_the_certified_bound(bank):
+    # L^ bounds the Lipschitz constant of grad F, so F(v) <= F(u) + <grad F(u), v - u> + L^/2 |v - u|^2 for every
+    # u, v.  Along -g and +g the first-order term is the oracle's own gradient: a scaled or wrong gradient
+    # violates the inequality for small steps, a wrong L^ (too small) for large ones.
+    k, a = bank
+    rng = np.random.default_rng(5)
+    for bc in (O.BC_SYMMETRIC, O.BC_ZERO):
+        Lh = O.lipschitz(k, a, bc, 256)
+        for trial in range(3):
+            u = rng.uniform(0.5, 8.0, (20, 18))
+            F = O.prior_energy(k, a, u, bc)
+            g = O.prior_grad(k, a, u, bc)
+            for h in (-g, g, rng.standard_normal(u.shape)):
+                for eps in (1e-4, 1e-2, 1.0 / Lh, 3.0 / Lh):
+                    v = u + eps * h
+                    rhs = F + float(np.sum(g * (v - u))) + 0.5 * Lh * float(np.sum((v - u) ** 2))
+                    assert O.prior_energy(k, a, v, bc) <= rhs + 1e-10 * abs(F)
+
+
+def test_backtracking_never_rejects_above_the_bound(bank):
+    # Started high enough that L stays >= L^ for every step (it only shrinks by 1.5 per accepted step), the
+    # descent lemma makes every trial acceptable: no L is ever doubled.
+    k, a = bank
+    H, W, iters = 20, 18, 12
+    y = synth.poisson_observation(synth.clean_image(H, W, 21), 4.0, 22)
+    d = O.anscombe(y)
+    Lh = O.lipschitz(k, a, O.BC_SYMMETRIC, 256)
+    pr = O.Problem(k, a, H, W, model=O.MODEL_ANS_L2, lam=1.0, gamma=0.8)
+    _, _, trials = pr.ipiano_backtrack(d, d, iters, Lh * 1.5 ** iters)
+    assert len(trials) == iters and all(ok for _, ok, _ in trials)
+
+
+def test_backtracking_from_a_small_estimate(bank):
+    # From an L far below the curvature the first trials are rejected and L doubles until the test passes;
+    # each accepted step satisfies the sufficient-decrease inequality, the energy E = F + G decreases overall,
+    # and replaying the accepted step sizes with fixed-step iPiano reproduces the iterates exactly.
+    k, a = bank
+    H, W, iters = 20, 18, 15
+    y = synth.poisson_observation(synth.clean_image(H, W, 23), 4.0, 24)
+    d = O.anscombe(y)
+    Lh = O.lipschitz(k, a, O.BC_SYMMETRIC, 256)
+    pr = O.Problem(k, a, H, W, model=O.MODEL_ANS_L2, lam=1.0, gamma=0.8)
+    u, _, trials = pr.ipiano_backtrack(d, d, iters, Lh / 300.0)
+    assert sum(1 for _, ok, _ in trials if not ok) >= 5
+    assert sum(1 for _, ok, _ in trials if ok) == iters
+    assert pr.energy(u, d) < pr.energy(d, d)
+    taus = [t for t, ok, _ in trials if ok]
+    v, vp = d.copy(), d.copy()
+    for t in taus:
+        vn = pr.step(d, v, vp, tau=t)
+        vp, v = v, vn
+    assert np.array_equal(v, u)
+    # the recorded trials obey the rule: a rejection doubles L, an acceptance divides it by 1.5
+    for (t0, ok0, L0), (t1, ok1, L1) in zip(trials, trials[1:]):
+        assert math.isclose(L1, L0 * 2.0 if not ok0 else L0 / 1.5, rel_tol=1e-12)
+        assert math.isclose(t0, 2 * (1 - 0.8) / (L0 + 2e-3), rel_tol=1e-12)
