@@ -462,6 +462,22 @@ def main():
         tf32 = {"value": job_value(pix_iters_step * args.fp32_steps, t3 / 1e3, world) / 1e6, "unit": "MPix·iter/s",
                 "ms_per_step": t3 / args.fp32_steps, "avg_launch_us": (l3 / 1e3) / max(n3, 1) * 1e6}
 
+    # step control by Lipschitz backtracking (FP32, one 512x512 image, 100 iterations, A2 model at peak 8): the
+    # host decides every trial, so this leg reports its wall time and the trial counts, not a throughput target
+    backtrack = None
+    if not args.main_only and rank == 0:
+        xb = torch.empty((H, ld), dtype=torch.float32, device=dev)
+        ob = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_FP32, step=F.FOE_STEP_BACKTRACK, iters=100)
+        F.foe_denoise(ctx, ys[8], xb, H, W, ld, 8.0, ob, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = F.foe_denoise(ctx, ys[8], xb, H, W, ld, 8.0, ob, stream=stream, report=True)
+        wall = time.perf_counter() - t0
+        tb, ab = F.foe_step_log(ctx)
+        backtrack = {"H": H, "W": W, "iters": 100, "prec": "fp32", "wall_ms": wall * 1e3, "trials": int(len(tb)),
+                     "rejected": int((~ab).sum()), "lipschitz_final": rb["lipschitz_final"],
+                     "mpix_iter_per_s": H * W * 100 / wall / 1e6}
+
     # single-image latency (one 512x512 image, 300 iterations, A2 model at peak 8)
     xs1 = torch.empty((H, ld), dtype=torch.float32, device=dev)
     for _ in range(2):
@@ -591,6 +607,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "tf32_tensor_core": tf32, "single_image_ms": float(np.median(lat)),
+                "backtrack": backtrack,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "train": train, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
