@@ -513,33 +513,47 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
         __syncthreads();
         if (tile + (int)gridDim.x < ntiles) stage_tile<MODE, TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
 
-        // ---- tile mean (BF16 range), then E ----
+        // ---- operand offset (BF16 range), then E ----
+        // Any constant c gives K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the
+        // mean of 64 samples of the region (an 8 x 8 grid) serves.
         const float *Ub = S.U[buf];
-        float lsum = 0.0f;
-        for (int r = warp; r < UR; r += NWARP)
-            for (int c = lane; c < UR; c += 32) lsum += Ub[r * UC + c];
-        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        if (lane == 0) S.red[warp] = lsum;
-        __syncthreads();
-        float mean = 0.0f;
+        if (warp == 0) {
+            float v = 0.0f;
 #pragma unroll
-        for (int w = 0; w < NWARP; ++w) mean += S.red[w];
-        mean *= 1.0f / (float)(UR * UR);
-        for (int j = tid; j < EROWS * RS; j += NTHR) {
-            const int i = j / RS, x = j % RS;
-            const float *src = &Ub[i * UC + x];
+            for (int h = 0; h < 2; ++h) {
+                const int sidx = lane + 32 * h;
+                v += Ub[(2 + 5 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
+            }
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) S.red[0] = v * (1.0f / 64.0f);
+        }
+        __syncthreads();
+        const float mean = S.red[0];
+        // one thread per 4 consecutive entries of an E row: the 11 inputs they span are loaded (three 16-byte
+        // loads), shifted and rounded once
+        for (int item = tid; item < EROWS * (RS / 4); item += NTHR) {
+            const int i = item / (RS / 4), x0 = 4 * (item % (RS / 4));
+            const float4 *src = reinterpret_cast<const float4 *>(&Ub[i * UC + x0]);
+            const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+            const float v[11] = {a0.x - mean, a0.y - mean, a0.z - mean, a0.w - mean, a1.x - mean, a1.y - mean,
+                                 a1.z - mean, a1.w - mean, a2.x - mean, a2.y - mean, a2.z - mean};
+            uint4 *dst = &S.E[0][i * RS + x0];
             if (TF) {
-                S.E[0][j] = make_uint4(to_tf32(src[0] - mean), to_tf32(src[1] - mean), to_tf32(src[2] - mean),
-                                       to_tf32(src[3] - mean));
-                S.E[TcOps<TF>::EB - 1][j] = make_uint4(to_tf32(src[4] - mean), to_tf32(src[5] - mean),
-                                                       to_tf32(src[6] - mean), to_tf32(src[7] - mean));
+                uint32_t c[11];
+#pragma unroll
+                for (int j2 = 0; j2 < 11; ++j2) c[j2] = to_tf32(v[j2]);
+                uint4 *dst1 = &S.E[TcOps<TF>::EB - 1][i * RS + x0];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    dst[e] = make_uint4(c[e], c[e + 1], c[e + 2], c[e + 3]);
+                    dst1[e] = make_uint4(c[e + 4], c[e + 5], c[e + 6], c[e + 7]);
+                }
             } else {
-                uint4 e;
-                e.x = pack_bf16x2(src[0] - mean, src[1] - mean);
-                e.y = pack_bf16x2(src[2] - mean, src[3] - mean);
-                e.z = pack_bf16x2(src[4] - mean, src[5] - mean);
-                e.w = pack_bf16x2(src[6] - mean, src[7] - mean);
-                S.E[0][j] = e;
+                uint32_t pr[10];
+#pragma unroll
+                for (int j2 = 0; j2 < 10; ++j2) pr[j2] = pack_bf16x2(v[j2], v[j2 + 1]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pr[e], pr[e + 2], pr[e + 4], pr[e + 6]);
             }
         }
         fence_async_smem();
