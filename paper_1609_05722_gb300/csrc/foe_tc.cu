@@ -80,16 +80,21 @@ constexpr int B_W = 10;      // filter operand images arrived (bulk copy)       
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
 constexpr int NBAR = 13;
 
+// Input-region / output-operand buffers: two for BF16 (the next tile is copied in during the current one), one
+// for TF32 (whose larger operand images leave room for only one if two CTAs are to share an SM).
+template <bool TF>
+constexpr int kNBuf = TF ? 1 : 2;
+
 template <bool TF>
 struct TcSmem {
     uint4 E[TcOps<TF>::EB][EROWS * RS];   // forward A operand: entry (row, x) holds u(row, x..x+7)
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
     float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
-    float U[2][UR * UC];        // fp32 input region (this tile / the next one, prefetched)
-    float O[2][3][TO * TO];     // output-pass operands [unused], delta, d (this tile / the next one)
-    int srow[2][UR], scol[2][UR];  // source row / column of each input-region row / column (-1: zero)
-    int geo[2][3];              // image, oy0, ox0 of the tile in buffer b
+    float U[kNBuf<TF>][UR * UC];        // fp32 input region (this tile / the next one)
+    float O[kNBuf<TF>][2][TO * TO];     // output-pass operands delta, d (this tile / the next one)
+    int srow[kNBuf<TF>][UR], scol[kNBuf<TF>][UR];  // source row / column of each region row / column (-1: zero)
+    int geo[kNBuf<TF>][3];              // image, oy0, ox0 of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -445,8 +450,8 @@ __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, i
             const int gy = oy0 + r, j = r * TO + lane;
             if (gy >= H || gx >= W) continue;
             const size_t idx = (size_t)gy * ld + gx;
-            if (MODE == kStep) cp_async4(&S.O[b][1][j], D.delta + idx);
-            cp_async4(&S.O[b][2][j], D.d + idx);
+            if (MODE == kStep) cp_async4(&S.O[b][0][j], D.delta + idx);
+            cp_async4(&S.O[b][1][j], D.d + idx);
         }
     }
     cp_async_commit();
@@ -455,7 +460,7 @@ __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, i
 // Persistent: CTA c processes tiles c, c + gridDim.x, ...; tensor memory, barriers and the filter operands
 // are set up once, and the input region of the next tile is copied in while the current one is computed.
 template <int MODE, bool TF>
-__global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
+__global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem<TF> &S = *reinterpret_cast<TcSmem<TF> *>(smem_raw);
@@ -503,15 +508,18 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
 
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        const int buf = k & 1;
+        constexpr int NB = kNBuf<TF>;
+        const int buf = NB == 2 ? (k & 1) : 0;
         const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2];
         const ImgDesc &D = A.img[im];
         const int H = D.H, W = D.W, ld = D.ld;
 
-        // this tile's copies (issued one tile earlier) have landed; start the next tile's
+        // this tile's copies (issued during the previous tile, or after it with one buffer) have landed; with two
+        // buffers, start the next tile's
         cp_async_wait<0>();
         __syncthreads();
-        if (tile + (int)gridDim.x < ntiles) stage_tile<MODE, TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+        if (NB == 2 && tile + (int)gridDim.x < ntiles)
+            stage_tile<MODE, TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
 
         // ---- operand offset (BF16 range), then E ----
         // Any constant c gives K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the
@@ -627,22 +635,30 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
                     if (!mbar_wait(&S.bar[B_FWD + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
                     fence_after();
                     const uint32_t rc = tmem + lane_base + 64 * (t & 1);
-                    float r[48];
-                    tmem_ld32(rc, r);
-                    tmem_ld16(rc + 32, r + 32);
-                    tmem_wait_ld();
                     const int gy = oy0 - 3 + 4 * t + q;
                     const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
                     if (TF) {
-                        uint32_t w[48];
+                        // Psi takes R's columns one for one: two halves of 24 filters keep the registers low
 #pragma unroll
-                        for (int j = 0; j < 48; ++j) {
-                            const float r0 = r[j];
-                            w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
+                        for (int hh = 0; hh < 2; ++hh) {
+                            float r[24];
+                            tmem_ld16(rc + 24 * hh, r);
+                            tmem_ld8(rc + 24 * hh + 16, r + 16);
+                            tmem_wait_ld();
+                            uint32_t w[24];
+#pragma unroll
+                            for (int j = 0; j < 24; ++j) {
+                                const float r0 = r[j];
+                                w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
+                            }
+                            tmem_st16(rc + 24 * hh, w);
+                            tmem_st8(rc + 24 * hh + 16, w + 16);
                         }
-                        tmem_st32(rc, w);
-                        tmem_st16(rc + 32, w + 32);
                     } else {
+                        float r[48];
+                        tmem_ld32(rc, r);
+                        tmem_ld16(rc + 32, r + 32);
+                        tmem_wait_ld();
                         uint32_t w[24];
 #pragma unroll
                         for (int j = 0; j < 24; ++j) w[j] = psi_bf16x2(r[2 * j], r[2 * j + 1]);
@@ -742,10 +758,10 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
                 const int r = warp + k2 * NWARP, j = r * TO + lane;
                 const size_t idx = (size_t)(oy0 + r) * ld + gx;
                 if (MODE == kGrad) {
-                    D.out[idx] = g[k2] + data_grad(uh[k2], S.O[buf][2][j], D.model, D.sc.lambda);
+                    D.out[idx] = g[k2] + data_grad(uh[k2], S.O[buf][1][j], D.model, D.sc.lambda);
                 } else {
                     float nh, nd;
-                    ipiano_update_f32(g[k2], uh[k2], S.O[buf][1][j], S.O[buf][2][j], D.model, D.sc, nh, nd);
+                    ipiano_update_f32(g[k2], uh[k2], S.O[buf][0][j], S.O[buf][1][j], D.model, D.sc, nh, nd);
                     D.u_hi[A.parity ^ 1][idx] = nh;
                     D.delta[idx] = nd;
                 }
@@ -755,6 +771,8 @@ __global__ void __launch_bounds__(NTHR, TF ? 1 : 2) k_foe_tc(const __grid_consta
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
+        if (NB == 1 && tile + (int)gridDim.x < ntiles)
+            stage_tile<MODE, TF>(A, S, tile + gridDim.x, 0, tid, warp, lane);
     }
 
     // every MMA issued by the two MMA threads is complete before tensor memory is released
@@ -810,8 +828,8 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // persistent CTAs: as many as are resident at once (tensor memory admits two per SM, one for TF32)
-    const int grid = std::min(tiles, (tf32 ? 1 : 2) * sms);
+    // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
+    const int grid = std::min(tiles, 2 * sms);
     if (tf32) {
         if (mode == kStep) k_foe_tc<kStep, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
         else k_foe_tc<kGrad, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
