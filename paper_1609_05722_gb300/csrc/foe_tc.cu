@@ -94,7 +94,7 @@ struct TcSmem {
     float U[kNBuf<TF>][UR * UC];        // fp32 input region (this tile / the next one)
     float O[kNBuf<TF>][2][TO * TO];     // output-pass operands delta, d (this tile / the next one)
     int srow[kNBuf<TF>][UR], scol[kNBuf<TF>][UR];  // source row / column of each region row / column (-1: zero)
-    int geo[kNBuf<TF>][3];              // image, oy0, ox0 of the tile in buffer b
+    int geo[kNBuf<TF>][4];              // image, oy0, ox0, write limit xe of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -409,14 +409,27 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
     return g;
 }
 
-// Image and origin of a tile.
-__device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0)
+// Image, origin and column write limit of a tile.  The horizontal col2im of a response row is formed across
+// the 32 lanes of a warp, so its sums exist only at region columns 0..31.  The padding fold of a pixel within 3
+// columns of the right border needs the sum at its reflection (up to column W + 2), which lies inside the region
+// only if the tile reaches that border: the last tile of a row is therefore placed flush right (origin W - 26)
+// and the tile before it writes only the columns left of that origin.  Rows need no such rule: the vertical part
+// of the col2im reads response rows, and the rows that a reflection asks for that lie in the image are always
+// within 3 rows of the output row.
+__device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0, int &xe)
 {
     im = tile_image(A, tile);
     const ImgDesc &D = A.img[im];
     const int lt = tile - A.tile_prefix[im];
+    const int tx = lt % D.tiles_x;
     oy0 = (lt / D.tiles_x) * TO;
-    ox0 = (lt % D.tiles_x) * TO;
+    ox0 = tx * TO;
+    xe = min(ox0 + TO, D.W);
+    if (D.W > TO) {
+        const int last = D.W - TO;
+        ox0 = min(ox0, last);
+        xe = tx + 1 < D.tiles_x ? min(xe, last) : D.W;
+    }
 }
 
 // Issue the asynchronous copies of a tile's input region and output-pass operands into buffer b (all threads;
@@ -425,7 +438,7 @@ template <int MODE, bool TF>
 __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
                                            int lane)
 {
-    if (tid == 0) tile_geometry(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2]);
+    if (tid == 0) tile_geometry(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
     __syncthreads();
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
@@ -510,7 +523,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         constexpr int NB = kNBuf<TF>;
         const int buf = NB == 2 ? (k & 1) : 0;
-        const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2];
+        const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3];
         const ImgDesc &D = A.img[im];
         const int H = D.H, W = D.W, ld = D.ld;
 
@@ -737,7 +750,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 const int r = warp + k2 * NWARP, yo = 3 + r, gy = oy0 + r;
-                ok_r[k2] = r < TO && gy < H && gx < W;
+                ok_r[k2] = r < TO && gy < H && gx < xe;
                 g[k2] = 0.0f;
                 uh[k2] = 0.0f;
                 if (ok_r[k2]) {
