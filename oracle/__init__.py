@@ -80,6 +80,10 @@ def lib() -> C.CDLL:
             L.orc_ipiano.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_int, _dp]
             L.orc_denoise.restype = C.c_int
             L.orc_denoise.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, _dp]
+            L.orc_bin3.argtypes = [C.c_int, C.c_int, _dp, _dp]
+            L.orc_upscale3.argtypes = [C.c_int, C.c_int, _dp, C.c_int, C.c_int, _dp]
+            L.orc_denoise_binned.restype = C.c_int
+            L.orc_denoise_binned.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, _dp]
             L.orc_lipschitz.restype = C.c_double
             L.orc_lipschitz.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int]
             L.orc_train_loss.restype = C.c_double
@@ -290,6 +294,31 @@ class Problem:
         x = np.empty_like(y)
         used = lib().orc_denoise(C.byref(self.p), _p(y), float(peak), float(zero_c), int(iters), _p(x))
         return x, used
+
+    def denoise_binned(self, y, peak, iters, zero_c=0.0):
+        """FoEPNRbin: bin3, denoise the binned image at 9 * peak, upscale3 (the problem's H, W are the full sizes)."""
+        y = _d(y)
+        x = np.empty_like(y)
+        used = lib().orc_denoise_binned(C.byref(self.p), _p(y), float(peak), float(zero_c), int(iters), _p(x))
+        return x, used
+
+
+# ---- binning variant (FoEPNRbin, Sec. 4) ----
+def bin3(y):
+    """Sums of the non-overlapping 3x3 bins, ceil(H/3) x ceil(W/3); a bin cut by the border is scaled by 9 / n."""
+    y = _d(y)
+    H, W = y.shape
+    yb = np.empty(((H + 2) // 3, (W + 2) // 3))
+    lib().orc_bin3(H, W, _p(y), _p(yb))
+    return yb
+
+
+def upscale3(xb, H, W):
+    """Bilinear interpolation of the bin image at ((r - 1) / 3, (c - 1) / 3), clamped to the edge bins, / 9."""
+    xb = _d(xb)
+    x = np.empty((int(H), int(W)))
+    lib().orc_upscale3(xb.shape[0], xb.shape[1], _p(xb), int(H), int(W), _p(x))
+    return x
 
 
 def lipschitz(k, alpha, bc=BC_SYMMETRIC, ngrid=512) -> float:

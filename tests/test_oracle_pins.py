@@ -440,3 +440,72 @@ def test_backtracking_from_a_small_estimate(bank):
     for (t0, ok0, L0), (t1, ok1, L1) in zip(trials, trials[1:]):
         assert math.isclose(L1, L0 * 2.0 if not ok0 else L0 / 1.5, rel_tol=1e-12)
         assert math.isclose(t0, 2 * (1 - 0.8) / (L0 + 2e-3), rel_tol=1e-12)
+
+
+# ---- binning variant (FoEPNRbin, Sec. 4: 3x3 ones-kernel bins, bilinear upscaling) ----
+@pytest.mark.parametrize("shape", [(9, 12), (8, 10), (7, 11)])
+def test_bin3_one_hot_positions_and_border_scaling(shape):
+    # a unit count at (r, c) lands in bin (r // 3, c // 3) alone, as 9 / n for a bin of n pixels (n < 9 only
+    # where the border cuts the bin): pins the bin grid, the sum and the border reading
+    H, W = shape
+    Hb, Wb = (H + 2) // 3, (W + 2) // 3
+    for r in range(H):
+        for c in range(W):
+            y = np.zeros((H, W))
+            y[r, c] = 1.0
+            yb = O.bin3(y)
+            assert yb.shape == (Hb, Wb)
+            I, J = r // 3, c // 3
+            n = min(3, H - 3 * I) * min(3, W - 3 * J)
+            want = np.zeros((Hb, Wb))
+            want[I, J] = 9.0 / n
+            np.testing.assert_array_equal(yb, want)
+
+
+def test_bin3_raises_the_peak_nine_fold():
+    # a constant image of c counts bins to 9c everywhere (border bins included); on a 3-divisible image the counts
+    # are preserved in total
+    np.testing.assert_array_equal(O.bin3(np.full((10, 14), 2.0)), np.full((4, 5), 18.0))
+    y = np.random.default_rng(3).poisson(1.5, (12, 15)).astype(float)
+    assert O.bin3(y).sum() == y.sum()
+
+
+def test_upscale3_equals_library_bilinear_interpolation():
+    # bilinear interpolation of the bin image at ((r - 1) / 3, (c - 1) / 3), clamped at the edges, is the order-1
+    # spline of scipy.ndimage.map_coordinates with mode "nearest"
+    from scipy import ndimage
+    rng = np.random.default_rng(5)
+    for H, W in [(21, 23), (19, 27), (30, 30)]:
+        xb = rng.uniform(0.0, 9.0, ((H + 2) // 3, (W + 2) // 3))
+        rr, cc = np.meshgrid((np.arange(H) - 1) / 3.0, (np.arange(W) - 1) / 3.0, indexing="ij")
+        want = ndimage.map_coordinates(xb, [rr, cc], order=1, mode="nearest") / 9.0
+        np.testing.assert_allclose(O.upscale3(xb, H, W), want, rtol=0, atol=1e-13)
+
+
+def test_upscale3_reproduces_affine_images_between_bin_centres():
+    # bin values sampled from an affine function at the bin centres (3I + 1, 3J + 1) come back as that function
+    # (divided by 9) at every pixel whose interpolation stencil lies between centres
+    H, W = 22, 25
+    Hb, Wb = (H + 2) // 3, (W + 2) // 3
+    f = lambda r, c: 9.0 * (0.7 + 0.11 * r - 0.05 * c)
+    I, J = np.meshgrid(np.arange(Hb), np.arange(Wb), indexing="ij")
+    x = O.upscale3(f(3 * I + 1.0, 3 * J + 1.0), H, W)
+    r, c = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    inside = (r >= 1) & (r <= 3 * (Hb - 1) + 1) & (c >= 1) & (c <= 3 * (Wb - 1) + 1)
+    np.testing.assert_allclose(x[inside], f(r, c)[inside] / 9.0, rtol=0, atol=1e-13)
+
+
+def test_denoise_binned_constant_image_and_binned_peak_threshold(bank):
+    # a constant image of c counts bins to the constant 9c, a stationary point of the prior (zero-mean filters) and
+    # of the quadratic data term at u = v: the result is I_C(2 sqrt(9c + 3/8)) / 9 everywhere.  The data term is
+    # chosen by the binned peak, 9 * peak, against the threshold 5 (Sec. 3.4).
+    k, a = bank
+    H, W = 20, 23
+    pr = O.Problem(k, a, H, W, model=O.MODEL_AUTO, lam=1.0, tau=1e-3, gamma=0.8, nthreads=1)
+    x, used = pr.denoise_binned(np.full((H, W), 3.0), 0.6, 20)
+    assert used == O.MODEL_ANS_L2
+    want = float(O.inverse(np.array([2.0 * math.sqrt(27.0 + 3.0 / 8.0)]))[0]) / 9.0
+    np.testing.assert_allclose(x, want, rtol=1e-12)
+    y = synth.poisson_observation(synth.clean_image(H, W, 19), 0.5, 20)
+    assert pr.denoise_binned(y, 0.5, 2)[1] == O.MODEL_ANS_IDIV
+    assert pr.denoise_binned(y, 5.0 / 9.0, 2)[1] == O.MODEL_ANS_L2
