@@ -159,6 +159,20 @@ FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted
 FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *opts, void *stream, foe_report *rep);
 
+/* The binning variant FoEPNRbin (Sec. 4: a 3x3 ones kernel raises the peak nine-fold before the solve, bilinear
+ * interpolation upscales the low-resolution estimate after it).  y is summed over the non-overlapping 3x3 bins
+ * starting at pixel (0, 0) (a bin cut by the image border, with n < 9 pixels, is scaled by 9 / n); the
+ * ceil(H/3) x ceil(W/3) bin image is denoised exactly as foe_denoise does, with peak 9 * peak (FOE_MODEL_AUTO
+ * applies the threshold 5 to that binned peak, Sec. 3.4); x(r, c) is the bilinear interpolation of the estimate
+ * at ((r - 1) / 3, (c - 1) / 3), bin (I, J) being centred on pixel (3I + 1, 3J + 1) and coordinates clamped to the
+ * edge bins, divided by 9.
+ *   y, x   device, H x W, pitch ld (floats), 16-byte aligned; H, W >= 19 (the bin image is at least 7 x 7)
+ *   peak   the peak of the full-resolution image
+ * The bin image and its estimate live in context memory (allocated on first use, grown as needed).  opts, the
+ * report and the errors are those of foe_denoise (the report describes the binned solve). */
+FOE_API foe_status foe_denoise_binned(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
+                                      const foe_solve_opts *opts, void *stream, foe_report *rep);
+
 /* foe_denoise for callers that cannot allocate device memory at the time of the call: code that runs
  * while a CUDA graph is being captured (cudaMalloc is not permitted under global capture), code whose
  * device memory is owned entirely by another allocator (a framework's caching allocator or a fixed

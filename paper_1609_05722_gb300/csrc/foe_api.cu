@@ -157,6 +157,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
     cudaFree(c->ws);
+    cudaFree(c->d_bin);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     delete c;
 }
@@ -348,6 +349,33 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
             return (foe_status)dev_status;
         }
     }
+    return FOE_OK;
+}
+
+foe_status foe_denoise_binned(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
+                              const foe_solve_opts *o, void *stream, foe_report *rep)
+{
+    if (!c) return FOE_EINVAL;
+    foe_status st;
+    if ((st = check_opts(c, o)) != FOE_OK) return st;
+    if ((st = check_image(c, y, H, W, ld, "y")) != FOE_OK) return st;
+    if ((st = check_image(c, x, H, W, ld, "x")) != FOE_OK) return st;
+    const int Hb = (H + 2) / 3, Wb = (W + 2) / 3, ldb = (Wb + 3) / 4 * 4;
+    if (Hb < 7 || Wb < 7) {
+        set_err(c, "foe_denoise_binned: the binned image must be at least 7 x 7 (H, W >= 19; got %d x %d)", H, W);
+        return FOE_EINVAL;
+    }
+    if (o->model == FOE_MODEL_AUTO && !(peak > 0.0f && std::isfinite(peak))) {
+        set_err(c, "peak must be > 0 for FOE_MODEL_AUTO");
+        return FOE_EINVAL;
+    }
+    const size_t plane = (size_t)Hb * ldb;
+    if ((st = ensure_bin(c, 2 * plane * sizeof(float))) != FOE_OK) return st;
+    float *yb = c->d_bin, *xb = c->d_bin + plane;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOE_CUDA(c, foe::launch_bin3(y, H, W, ld, yb, ldb, s));
+    if ((st = foe_denoise(c, yb, xb, Hb, Wb, ldb, 9.0f * peak, o, stream, rep)) != FOE_OK) return st;
+    FOE_CUDA(c, foe::launch_upscale3(xb, ldb, x, H, W, ld, s));
     return FOE_OK;
 }
 

@@ -28,6 +28,8 @@ struct foe_ctx {
     void *d_tcops32 = nullptr;              // device, the same in tf32 (24 KB)
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    float *d_bin = nullptr;                 // foe_denoise_binned: the bin image and its estimate
+    size_t bin_bytes = 0;
     double *d_partials = nullptr;
     int partials_cap = 0;
     double *d_energy = nullptr;
@@ -294,6 +296,17 @@ inline foe_status ensure_ws(foe_ctx *c, size_t bytes)
     c->ws_bytes = 0;
     FOE_CUDA(c, cudaMalloc(&c->ws, bytes));
     c->ws_bytes = bytes;
+    return FOE_OK;
+}
+
+inline foe_status ensure_bin(foe_ctx *c, size_t bytes)
+{
+    if (bytes <= c->bin_bytes) return FOE_OK;
+    if (c->d_bin) FOE_CUDA(c, cudaFree(c->d_bin));
+    c->d_bin = nullptr;
+    c->bin_bytes = 0;
+    FOE_CUDA(c, cudaMalloc(&c->d_bin, bytes));
+    c->bin_bytes = bytes;
     return FOE_OK;
 }
 

@@ -40,6 +40,11 @@ cudaError_t launch_anscombe(const float *y, float *v, long n, cudaStream_t s);
 cudaError_t launch_inverse(const float *z, float *x, long n, cudaStream_t s);
 cudaError_t launch_reduce(const double *p, int n, double *out, cudaStream_t s);
 
+// Binning variant (foe_bin.cu): yb = ceil(H/3) x ceil(W/3) bin sums of y (pitch ldb); x = the bilinear upscaling of
+// the bin image xb (pitch ldb) to H x W (pitch ld), divided by 9.
+cudaError_t launch_bin3(const float *y, int H, int W, int ld, float *yb, int ldb, cudaStream_t s);
+cudaError_t launch_upscale3(const float *xb, int ldb, float *x, int H, int W, int ld, cudaStream_t s);
+
 // Step control (foe_backtrack.cu): out[0] = sum g * dl, out[1] = sum dl * dl over an H x W plane (pitch ld),
 // FP64, in a fixed order (per-block partials in `partials`, 2 * dot2_blocks(H) doubles, then one block).
 int dot2_blocks(int H);

@@ -82,6 +82,7 @@ def lib() -> C.CDLL:
             "foe_prior_lipschitz": (i, [C.POINTER(foe_prior), i, C.POINTER(d)]),
             "foe_step_log": (i, [vp, C.POINTER(f), C.POINTER(C.c_ubyte), i]),
             "foe_denoise": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
+            "foe_denoise_binned": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
             "foe_denoise_batch": (i, [vp, C.POINTER(foe_image_desc), i, C.POINTER(foe_solve_opts), vp]),
             "foe_energy_grad": (i, [vp, vp, vp, i, i, i, i, f, i, i, C.POINTER(d), vp, vp]),
             "foe_ipiano_step": (i, [vp, vp, vp, vp, vp, vp, i, i, i, i, f, f, f, i, i, vp]),
@@ -212,6 +213,19 @@ def foe_denoise(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts
     rep = foe_report()
     _check(lib().foe_denoise(ctx, _ptr(y), _ptr(x), H, W, ld, peak, C.byref(o), _stream(stream),
                              C.byref(rep) if report else None), ctx, "foe_denoise")
+    if report:
+        return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
+                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final}
+    return None
+
+
+def foe_denoise_binned(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts | None = None, stream=None,
+                       report: bool = False):
+    """The binning variant (3x3 bin sums, solve at 9 * peak, bilinear upscaling); arguments as foe_denoise."""
+    o = (opts or SolveOpts()).c()
+    rep = foe_report()
+    _check(lib().foe_denoise_binned(ctx, _ptr(y), _ptr(x), H, W, ld, peak, C.byref(o), _stream(stream),
+                                    C.byref(rep) if report else None), ctx, "foe_denoise_binned")
     if report:
         return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
                 "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final}
