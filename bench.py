@@ -494,6 +494,33 @@ def main():
         e1.synchronize()
         lat.append(e0.elapsed_time(e1))
 
+    # binning variant (3x3 bins, solve at 9x peak, bilinear upscaling) on one 512x512 image at peak 0.5, the regime
+    # the paper bins in: 300 iterations on the 171x171 bin image, against the same image solved at full size
+    binned = None
+    if not args.main_only and rank == 0:
+        pk = 0.5
+        yb_img = torch.from_numpy(synth.poisson_observation(synth.clean_image(H, W, 1200), pk, 6200)
+                                  .astype(np.float32)).to(dev)
+        yb_full = torch.zeros((H, ld), dtype=torch.float32, device=dev)
+        yb_full[:, :W] = yb_img
+        xb = torch.empty((H, ld), dtype=torch.float32, device=dev)
+        ob = F.SolveOpts(model=F.FOE_MODEL_AUTO, prec=prec_main, iters=ITERS)
+        tb = {}
+        for name, fn in (("binned", F.foe_denoise_binned), ("full", F.foe_denoise)):
+            for _ in range(3):
+                fn(ctx, yb_full, xb, H, W, ld, pk, ob, stream=stream)
+            ts = []
+            for _ in range(5):
+                flush.zero_()
+                e0.record(stream)
+                fn(ctx, yb_full, xb, H, W, ld, pk, ob, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            tb[name] = float(np.median(ts))
+        binned = {"H": H, "W": W, "peak": pk, "iters": ITERS, "bin_image": [(H + 2) // 3, (W + 2) // 3],
+                  "binned_ms": tb["binned"], "full_ms": tb["full"]}
+
     # end to end through the public API: pinned host -> device, solve, device -> pinned host, each step
     xs_host = [torch.empty((H, ld), dtype=torch.float32).pin_memory() for _ in range(10)]
     ybuf = [torch.empty((H, ld), dtype=torch.float32, device=dev) for _ in range(10)]
@@ -607,7 +634,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "tf32_tensor_core": tf32, "single_image_ms": float(np.median(lat)),
-                "backtrack": backtrack,
+                "backtrack": backtrack, "binned": binned,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "train": train, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
