@@ -90,6 +90,12 @@ def lib() -> C.CDLL:
             L.orc_train_loss.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, C.c_int]
             L.orc_train_grad.restype = C.c_double
             L.orc_train_grad.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, C.c_int, _dp, _dp]
+            L.orc_hvp.argtypes = [C.POINTER(Params), _dp, _dp, _dp]
+            L.orc_cg.restype = C.c_int
+            L.orc_cg.argtypes = [C.POINTER(Params), _dp, _dp, C.c_int, C.c_double, _dp, _dp]
+            L.orc_train_grad_implicit.restype = C.c_double
+            L.orc_train_grad_implicit.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double,
+                                                  _dp, _dp, C.POINTER(C.c_int), _dp]
             L.orc_psnr.restype = C.c_double
             L.orc_psnr.argtypes = [C.c_long, _dp, _dp, C.c_double]
             _lib = L
@@ -288,6 +294,33 @@ class Problem:
         da = np.empty(self.k.shape[0])
         L = lib().orc_train_grad(C.byref(self.p), c.shape[0], _p(c), _p(y), int(T), _p(dk), _p(da))
         return L, dk.reshape(-1, 7, 7), da
+
+    def hvp(self, w, x):
+        """H_E(w) x for the Anscombe quadratic model: sum_i alpha_i K_i^T diag(rho''(K_i w)) K_i x + lambda x."""
+        w, x = _d(w), _d(x)
+        out = np.empty_like(w)
+        lib().orc_hvp(C.byref(self.p), _p(w), _p(x), _p(out))
+        return out
+
+    def cg(self, w, b, max_cg, tol):
+        """q ~ H_E(w)^{-1} b by conjugate gradients from 0: (q, iterations, relative residual)."""
+        w, b = _d(w), _d(b)
+        q = np.empty_like(w)
+        rel = np.zeros(1)
+        it = lib().orc_cg(C.byref(self.p), _p(w), _p(b), int(max_cg), float(tol), _p(q), _p(rel))
+        return q, it, float(rel[0])
+
+    def train_grad_implicit(self, clean, noisy, T, max_cg, tol):
+        """(loss, dL/dk (nf, 7, 7), dL/d log alpha (nf,), max CG iterations, max relative residual) by Eq.
+        implicitdifferentiation at u^T (T iPiano steps) for a batch of images (leading axis)."""
+        c, y = _d(clean), _d(noisy)
+        dk = np.empty((self.k.shape[0], 49))
+        da = np.empty(self.k.shape[0])
+        it = C.c_int(0)
+        rel = np.zeros(1)
+        L = lib().orc_train_grad_implicit(C.byref(self.p), c.shape[0], _p(c), _p(y), int(T), int(max_cg), float(tol),
+                                          _p(dk), _p(da), C.byref(it), _p(rel))
+        return L, dk.reshape(-1, 7, 7), da, it.value, float(rel[0])
 
     def denoise(self, y, peak, iters, zero_c=0.0):
         y = _d(y)

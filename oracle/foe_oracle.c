@@ -626,3 +626,136 @@ done:
     free(v); free(U); free(gb1); free(gb2); free(w); free(r); free(sv); free(psi); free(Hw); free(pu); free(pw);
     return L;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * The paper's own training gradient (Sec. 2.5, Eq. implicitdifferentiation and Eq. overallderivative), for the
+ * Anscombe quadratic model E(w) = E_FoE(w) + lambda/2 ||w - v||^2 and the loss of Sec. 3.2:
+ *   q = H_E(w*)^{-1} dL/dw at the minimiser w*,
+ *   H_E(w) = sum_i alpha_i K_i^T Gamma_i K_i + lambda I,   Gamma_i = diag(rho''(K_i w))        (Sec. 2.5),
+ *   dL/da_i      = -alpha_i (K_i^T rho'(K_i w*))^T q = -alpha_i sum_p (K_i q)_p rho'(r_i(p)),
+ *   dL/dk_i(a,b) = -alpha_i sum_p [ (P q)(p - (a,b)) rho'(r_i(p)) + (K_i q)_p rho''(r_i(p)) (P w*)(p - (a,b)) ],
+ * with r_i = K_i w* and the filter coefficients themselves as parameters (the basis B of Eq. filtercoe is the
+ * identity).  w* is approximated by T iPiano steps from v; q by conjugate gradients from q = 0, stopped when
+ * ||dL/dw - H_E q|| <= tol ||dL/dw|| or after max_cg iterations, or when p^T H_E p <= 0 (H_E is positive definite
+ * at a strict minimiser; elsewhere the solve stops there).
+ * ---------------------------------------------------------------------------------------- */
+/* out = H_E(w) x */
+void orc_hvp(const orc_params *p, const double *w, const double *x, double *out)
+{
+    const int nf = p->nf;
+    const long N = (long)p->H * p->W;
+    double *r = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *sv = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    if (!r || !sv) { free(r); free(sv); return; }
+    orc_responses(nf, p->k, p->H, p->W, w, p->bc, r, p->nthreads);
+    orc_responses(nf, p->k, p->H, p->W, x, p->bc, sv, p->nthreads);
+    for (int f = 0; f < nf; ++f)
+        for (long q = 0; q < N; ++q) sv[(size_t)f * N + q] *= p->alpha[f] * orc_rho2(r[(size_t)f * N + q]);
+    orc_adjoint(nf, p->k, p->H, p->W, sv, p->bc, out, p->nthreads);
+    for (long q = 0; q < N; ++q) out[q] += p->lambda * x[q];
+    free(r);
+    free(sv);
+}
+
+static double orc_dot(long n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Conjugate gradients for H_E(w) q = b from q = 0; returns the iterations taken, *relres = ||b - H q|| / ||b||
+ * from the recurrence. */
+int orc_cg(const orc_params *p, const double *w, const double *b, int max_cg, double tol, double *q, double *relres)
+{
+    const long N = (long)p->H * p->W;
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    double *Ad = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!r || !d || !Ad) { free(r); free(d); free(Ad); return -1; }
+    for (long i = 0; i < N; ++i) {
+        q[i] = 0.0;
+        r[i] = b[i];
+        d[i] = b[i];
+    }
+    const double rr0 = orc_dot(N, r, r);
+    double rr = rr0;
+    int it = 0;
+    while (it < max_cg && rr > tol * tol * rr0) {
+        orc_hvp(p, w, d, Ad);
+        const double dAd = orc_dot(N, d, Ad);
+        if (!(dAd > 0.0)) break;
+        const double al = rr / dAd;
+        for (long i = 0; i < N; ++i) {
+            q[i] += al * d[i];
+            r[i] -= al * Ad[i];
+        }
+        const double rr1 = orc_dot(N, r, r);
+        const double be = rr1 / rr;
+        for (long i = 0; i < N; ++i) d[i] = r[i] + be * d[i];
+        rr = rr1;
+        ++it;
+    }
+    if (relres) *relres = rr0 > 0.0 ? sqrt(rr / rr0) : 0.0;
+    free(r);
+    free(d);
+    free(Ad);
+    return it;
+}
+
+double orc_train_grad_implicit(const orc_params *p, int B, const double *clean, const double *noisy, int T,
+                               int max_cg, double tol, double *dk, double *dlogalpha, int *cg_iters_max,
+                               double *relres_max)
+{
+    const int nf = p->nf, H = p->H, W = p->W;
+    const long N = (long)H * W, PW = W + 2 * ORC_R, PN = (long)(H + 2 * ORC_R) * PW;
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+    double *U = (double *)malloc(sizeof(double) * (size_t)N * (T + 1));
+    double *b = (double *)malloc(sizeof(double) * (size_t)N);
+    double *q = (double *)malloc(sizeof(double) * (size_t)N);
+    double *r = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *sv = (double *)malloc(sizeof(double) * (size_t)nf * N);
+    double *pw = (double *)malloc(sizeof(double) * (size_t)PN);
+    double *pq = (double *)malloc(sizeof(double) * (size_t)PN);
+    double L = NAN;
+    int itmax = 0;
+    double rmax = 0.0;
+    if (!v || !U || !b || !q || !r || !sv || !pw || !pq) goto done;
+    for (int i = 0; i < nf * ORC_KK; ++i) dk[i] = 0.0;
+    for (int i = 0; i < nf; ++i) dlogalpha[i] = 0.0;
+    L = 0.0;
+    for (int s = 0; s < B; ++s) {
+        orc_train_forward(p, noisy + (size_t)s * N, T, v, U);
+        const double *w = U + (size_t)T * N;
+        L += orc_loss_one(w, clean + (size_t)s * N, N, b);
+        double rel = 0.0;
+        const int it = orc_cg(p, w, b, max_cg, tol, q, &rel);
+        if (it > itmax) itmax = it;
+        if (rel > rmax) rmax = rel;
+        orc_responses(nf, p->k, H, W, w, p->bc, r, p->nthreads);
+        orc_responses(nf, p->k, H, W, q, p->bc, sv, p->nthreads);
+        orc_pad_image(H, W, w, p->bc, pw);
+        orc_pad_image(H, W, q, p->bc, pq);
+        for (int f = 0; f < nf; ++f) {
+            const double *rf = r + (size_t)f * N, *sf = sv + (size_t)f * N;
+            double ga = 0.0;
+            for (long k = 0; k < N; ++k) ga += sf[k] * orc_rho1(rf[k]);
+            dlogalpha[f] += -p->alpha[f] * ga;
+            for (int a = -ORC_R; a <= ORC_R; ++a)
+                for (int bb = -ORC_R; bb <= ORC_R; ++bb) {
+                    double gk = 0.0;
+                    for (long y = 0; y < H; ++y)
+                        for (long x = 0; x < W; ++x) {
+                            const long k = y * W + x, pi = (y - a + ORC_R) * PW + (x - bb + ORC_R);
+                            gk += pq[pi] * orc_rho1(rf[k]) + sf[k] * orc_rho2(rf[k]) * pw[pi];
+                        }
+                    dk[(size_t)f * ORC_KK + (a + ORC_R) * ORC_KS + (bb + ORC_R)] += -p->alpha[f] * gk;
+                }
+        }
+    }
+done:
+    if (cg_iters_max) *cg_iters_max = itmax;
+    if (relres_max) *relres_max = rmax;
+    free(v); free(U); free(b); free(q); free(r); free(sv); free(pw); free(pq);
+    return L;
+}

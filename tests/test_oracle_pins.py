@@ -509,3 +509,72 @@ def test_denoise_binned_constant_image_and_binned_peak_threshold(bank):
     y = synth.poisson_observation(synth.clean_image(H, W, 19), 0.5, 20)
     assert pr.denoise_binned(y, 0.5, 2)[1] == O.MODEL_ANS_IDIV
     assert pr.denoise_binned(y, 5.0 / 9.0, 2)[1] == O.MODEL_ANS_L2
+
+
+# ------------------------------------- the paper's training gradient by implicit differentiation (Sec. 2.5)
+
+def _small_training_problem(bank, H=8, W=9, nf=6, lam=1.0, gamma=0.8, bc=O.BC_SYMMETRIC):
+    k, a = bank
+    k, a = k[:nf].copy(), a[:nf].copy()
+    tau = 0.99 * 2 * (1 - gamma) / (O.lipschitz(k, a, bc) + 2e-3)
+    return k, a, tau, O.Problem(k, a, H, W, bc=bc, model=O.MODEL_ANS_L2, lam=lam, tau=tau, gamma=gamma, nthreads=1)
+
+
+@pytest.mark.parametrize("bc", [O.BC_SYMMETRIC, O.BC_ZERO])
+def test_hessian_vector_product_matches_gradient_differences(bank, bc):
+    # H_E(w) x = d/dt grad E(w + t x) at t = 0 (central differences of the oracle's gradient, FP64)
+    k, a, tau, pr = _small_training_problem(bank, H=10, W=9, bc=bc)
+    rng = np.random.default_rng(8)
+    d = O.anscombe(rng.poisson(3.0, (10, 9)).astype(float))
+    w = d + rng.normal(0.0, 0.3, d.shape)
+    x = rng.standard_normal(d.shape)
+    eps = 1e-5
+    fd = (pr.energy_grad(w + eps * x, d)[1] - pr.energy_grad(w - eps * x, d)[1]) / (2 * eps)
+    hv = pr.hvp(w, x)
+    assert np.abs(hv - fd).max() <= 1e-6 * np.abs(hv).max()
+
+
+def test_conjugate_gradients_match_a_dense_solve(bank):
+    # H_E assembled column by column from the product and solved by LAPACK; CG from 0 reaches the same q
+    k, a, tau, pr = _small_training_problem(bank, H=8, W=9)
+    rng = np.random.default_rng(9)
+    w = O.anscombe(rng.poisson(3.0, (8, 9)).astype(float))
+    n = w.size
+    Hd = np.stack([pr.hvp(w, np.eye(n)[j].reshape(w.shape)).ravel() for j in range(n)], axis=1)
+    assert np.abs(Hd - Hd.T).max() <= 1e-12 * np.abs(Hd).max()
+    b = rng.standard_normal(w.shape)
+    q, it, rel = pr.cg(w, b, 500, 1e-13)
+    assert rel <= 1e-13 and it <= 500
+    np.testing.assert_allclose(q.ravel(), np.linalg.solve(Hd, b.ravel()), rtol=0, atol=1e-10 * np.abs(q).max())
+
+
+def test_implicit_gradient_is_the_derivative_of_the_loss_at_the_minimiser(bank):
+    # Eq. implicitdifferentiation / overallderivative at a tightly converged minimiser against (i) central
+    # differences of the loss of the converged solve along random parameter directions and (ii) the unrolled
+    # reverse-mode gradient of the same T steps, which tends to it as T grows
+    k, a, tau, pr = _small_training_problem(bank)
+    H, W, T, B = 8, 9, 3000, 2
+    clean = np.stack([synth.clean_image(H, W, 50 + s) * 4.0 for s in range(B)])
+    noisy = np.stack([synth.poisson_observation(clean[s] / 4.0, 4.0, 60 + s) for s in range(B)])
+    L, dk, da, it, rel = pr.train_grad_implicit(clean, noisy, T, 400, 1e-13)
+    assert rel <= 1e-12
+    assert L == pytest.approx(pr.train_loss(clean, noisy, T), rel=1e-14)
+    Lu, dku, dau = pr.train_grad(clean, noisy, T)
+    g_imp = np.concatenate([dk.ravel(), da])
+    g_unr = np.concatenate([dku.ravel(), dau])
+    assert np.abs(g_imp - g_unr).max() <= 1e-7 * np.abs(g_imp).max()
+    rng = np.random.default_rng(22)
+    eps = 1e-4
+    for _ in range(3):
+        dkd = rng.standard_normal(k.shape)
+        dad = rng.standard_normal(a.shape)
+        nrm = np.sqrt((dkd ** 2).sum() + (dad ** 2).sum())
+        dkd, dad = dkd / nrm, dad / nrm
+
+        def loss_at(t):
+            q = O.Problem(k + t * dkd, a * np.exp(t * dad), H, W, model=O.MODEL_ANS_L2, lam=1.0, tau=tau, gamma=0.8,
+                          nthreads=1)
+            return q.train_loss(clean, noisy, T)
+        fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
+        an = float((dk * dkd).sum() + (da * dad).sum())
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-10)
