@@ -223,6 +223,31 @@ FOE_API foe_status foe_train_step(foe_ctx *ctx, const float *clean, const float 
                                   const foe_solve_opts *opts, int ckpt_every, double *loss_host, float *dfilters,
                                   float *dlogalpha, void *stream);
 
+typedef struct {
+    int cg_iters;       /* largest number of conjugate-gradient iterations over the images */
+    double cg_relres;   /* largest final relative residual ||dL/dw - H_E q|| / ||dL/dw|| (CG recurrence, FP64) */
+    int breakdowns;     /* images whose CG stopped at p^T H_E p <= 0 (H_E not positive definite there) */
+} foe_implicit_report;
+
+/* The paper's own gradient of the same objective (Sec. 2.5, Eq. implicitdifferentiation and Eq.
+ * overallderivative): at the minimiser w* of the lower-level problem (approximated by u^T, T = opts->iters
+ * iPiano steps from v),
+ *     q = H_E(w*)^{-1} dL/dw,   H_E = sum_i alpha_i K_i^T diag(rho''(K_i w*)) K_i + lambda I,
+ *     dL/da_i = -alpha_i <K_i q, rho'(K_i w*)>,
+ *     dL/dk_i(a, b) = -alpha_i sum_p [ (P q)(p - (a,b)) rho'(r_i(p)) + (K_i q)_p rho''(r_i(p)) (P w*)(p - (a,b)) ],
+ * with q by conjugate gradients on the device from q = 0 (FP32 vectors, FP64 dot products in a fixed order;
+ * at most max_cg iterations, per image until ||dL/dw - H_E q|| <= cg_tol ||dL/dw||).  The filter coefficients
+ * are the parameters (the basis of Eq. filtercoe is the identity).  Unlike foe_train_step this needs no stored
+ * iterates: memory is 10 planes per image whatever T is.  It equals the unrolled gradient as T grows (when the
+ * iteration converges) and is exact only at a minimiser.
+ *   clean, noisy, opts, loss_host, dfilters, dlogalpha  as foe_train_step
+ *   max_cg >= 1, cg_tol >= 0 (0: run max_cg iterations)
+ *   rep      host, nullable: CG iterations and residuals (synchronises the stream) */
+FOE_API foe_status foe_train_grad_implicit(foe_ctx *ctx, const float *clean, const float *noisy, int B, int H, int W,
+                                           int ld, const foe_solve_opts *opts, int max_cg, float cg_tol,
+                                           double *loss_host, float *dfilters, float *dlogalpha,
+                                           foe_implicit_report *rep, void *stream);
+
 /* One iPiano step (Eq. iPianoupdate) on a state given explicitly, for callers that drive the loop:
  *   u_hi, u_lo   device, the iterate u^n = u_hi + u_lo (u_lo may be NULL = zeros; written if not NULL)
  *   delta        device, u^n - u^{n-1} (read, then overwritten with u^{n+1} - u^n)

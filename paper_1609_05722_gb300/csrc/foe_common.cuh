@@ -73,6 +73,7 @@ struct BwdArgs {
     int bc;
     int nchunks;
     int write_g;               // 0 at the last reverse step (gbar^0 is not needed)
+    int hvp_only;              // 1: gout only (no parameter partials; partials may be null)
     float tau, gamma, c1;      // c1 = 1 / (1 + tau lambda)
     const float *wts;          // device [48][49], correlation form
     const float *alpha;        // device [48]

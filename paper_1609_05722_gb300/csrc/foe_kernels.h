@@ -40,6 +40,21 @@ cudaError_t launch_anscombe(const float *y, float *v, long n, cudaStream_t s);
 cudaError_t launch_inverse(const float *z, float *x, long n, cudaStream_t s);
 cudaError_t launch_reduce(const double *p, int n, double *out, cudaStream_t s);
 
+// Conjugate gradients of the implicit-differentiation gradient (foe_implicit.cu), B images of H x W (pitch ld,
+// image stride H * ld).  part arrays hold kCgBlocks FP64 partials per image.
+constexpr int kCgBlocks = 64;
+struct CgState {
+    double rr[2];      // <r, r> at iteration k (slot k & 1)
+    double rr0;        // <b, b>
+    int done[2];       // stopped before iteration k (slot k & 1)
+    int iters;         // iterations taken
+    int breakdown;     // stopped at <p, H_E p> <= 0
+};
+cudaError_t launch_cg_dot(const float *a, const float *c, int B, int H, int W, int ld, double *part, cudaStream_t s);
+cudaError_t launch_cg_init(const double *part, CgState *st, int B, cudaStream_t s);
+cudaError_t launch_cg_update(float *q, float *r, float *p, const float *Ap, int B, int H, int W, int ld,
+                             const double *part_pap, double *part_rr, CgState *st, int k, double tol2, cudaStream_t s);
+
 // Binning variant (foe_bin.cu): yb = ceil(H/3) x ceil(W/3) bin sums of y (pitch ldb); x = the bilinear upscaling of
 // the bin image xb (pitch ldb) to H x W (pitch ld), divided by 9.
 cudaError_t launch_bin3(const float *y, int H, int W, int ld, float *yb, int ldb, cudaStream_t s);

@@ -1,4 +1,6 @@
 // Backward pass of the unrolled iPiano solve (training of the FoE prior, Sec. 2.5; loss of Sec. 3.2), FP32.
+// With hvp_only set, the same kernel is the Hessian-vector product of the implicit-differentiation gradient:
+// tau = -1, gamma = lambda - 1, c1 = 1 and no gbar^{n+2} give gout = lambda w + H(u) w = H_E(u) w.
 //
 // One launch handles one step n of the reverse sweep for a batch of images.  With w = c1 gbar^{n+1}
 // (c1 = 1/(1 + tau lambda), the derivative of the quadratic prox of Eq. subproblemGL2), each CTA computes
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_foe_bwd(const __grid_constant__
     const int lt = tile - A.tile_prefix[im];
     const int ty0 = (lt / D.tiles_x) * T, tx0 = (lt % D.tiles_x) * T;
     const int H = D.H, W = D.W, ld = D.ld;
-    float *part = A.partials + (size_t)tile * kBwdPartials;
+    float *part = A.hvp_only ? nullptr : A.partials + (size_t)tile * kBwdPartials;
 
     for (int j = tid; j < 6 * kKK * CH; j += NTHREADS) {
         const int c = j / (kKK * CH), t = (j / CH) % kKK, f = j % CH;
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_foe_bwd(const __grid_constant__
             if (lane == 0) S.ared[warp][f] = v;
         }
         __syncthreads();
-        if (tid < CH) {
+        if (!A.hvp_only && tid < CH) {
             float v = 0.0f;
             for (int w8 = 0; w8 < NTHREADS / 32; ++w8) v += S.ared[w8][tid];
             part[kNF * kKK + ch * CH + tid] = v;
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_foe_bwd(const __grid_constant__
         }
 
         // ---- filter gradient: warp = filter of the chunk, lane = column ----
-        {
+        if (!A.hvp_only) {
             const int f = warp;
             float g[kKS][kKS];
 #pragma unroll

@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
             "foe_server_poll": (i, [vp, C.POINTER(C.c_longlong), i, C.POINTER(i)]),
             "foe_server_get_stats": (i, [vp, C.POINTER(foe_server_stats)]),
             "foe_train_step": (i, [vp, vp, vp, i, i, i, i, C.POINTER(foe_solve_opts), i, C.POINTER(d), vp, vp, vp]),
+            "foe_train_grad_implicit": (i, [vp, vp, vp, i, i, i, i, C.POINTER(foe_solve_opts), i, f, C.POINTER(d), vp,
+                                            vp, C.POINTER(foe_implicit_report), vp]),
             "foe_profile": (i, [vp, i]),
             "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
             "foe_status_string": (C.c_char_p, [i]),
@@ -343,6 +345,22 @@ def foe_server_get_stats(srv) -> dict:
     s = foe_server_stats()
     _check(lib().foe_server_get_stats(srv, C.byref(s)), what="foe_server_get_stats")
     return {k: getattr(s, k) for k, _ in foe_server_stats._fields_}
+
+
+class foe_implicit_report(C.Structure):
+    _fields_ = [("cg_iters", C.c_int), ("cg_relres", C.c_double), ("breakdowns", C.c_int)]
+
+
+def foe_train_grad_implicit(ctx, clean, noisy, B: int, H: int, W: int, ld: int, opts: SolveOpts, dfilters, dlogalpha,
+                            max_cg: int = 200, cg_tol: float = 1e-5, stream=None):
+    """Loss and gradients by implicit differentiation at u^T (see include/foe.h); returns (loss, report dict)."""
+    loss = C.c_double()
+    rep = foe_implicit_report()
+    o = opts.c()
+    _check(lib().foe_train_grad_implicit(ctx, _ptr(clean), _ptr(noisy), B, H, W, ld, C.byref(o), int(max_cg),
+                                         float(cg_tol), C.byref(loss), _ptr(dfilters), _ptr(dlogalpha), C.byref(rep),
+                                         _stream(stream)), ctx, "foe_train_grad_implicit")
+    return loss.value, {"cg_iters": rep.cg_iters, "cg_relres": rep.cg_relres, "breakdowns": rep.breakdowns}
 
 
 def foe_train_step(ctx, clean, noisy, B: int, H: int, W: int, ld: int, opts: SolveOpts, dfilters, dlogalpha,

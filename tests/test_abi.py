@@ -27,7 +27,8 @@ def declared_symbols():
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
-    for required in ("foe_create", "foe_destroy", "foe_denoise", "foe_denoise_batch", "foe_denoise_binned", "foe_energy_grad",
+    for required in ("foe_create", "foe_destroy", "foe_denoise", "foe_denoise_batch", "foe_denoise_binned",
+                     "foe_train_grad_implicit", "foe_energy_grad",
                      "foe_status_string"):
         assert required in names
 
