@@ -611,6 +611,19 @@ def main():
                  "loss": tloss, "grad_norm": float(torch.linalg.vector_norm(dkg)),
                  "unrolled_mpix_iter_per_s": TB * TH * TW * TT / (float(np.median(tt)) / 1e3) / 1e6,
                  "precision": "fp32 forward, recompute and backward"}
+        # the paper's own gradient (implicit differentiation at u^T, conjugate gradients to 1e-5) on the same batch
+        dki = torch.zeros_like(dkg)
+        dai = torch.zeros_like(dag)
+        F.foe_train_grad_implicit(ctx, cl, nz, TB, TH, TW, tld, topts, dki, dai, 200, 1e-5, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iloss, irep = F.foe_train_grad_implicit(ctx, cl, nz, TB, TH, TW, tld, topts, dki, dai, 200, 1e-5, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        train["implicit"] = {"ms_per_step": e0.elapsed_time(e1), "cg_iters": irep["cg_iters"],
+                             "cg_relres": irep["cg_relres"], "breakdowns": irep["breakdowns"],
+                             "grad_norm": float(torch.linalg.vector_norm(dki))}
         del cl, nz
 
     # serving leg: continuous batching under a 40 GB budget vs the plain per-request paths
