@@ -41,3 +41,81 @@ class FoEUnrolledLoss(torch.autograd.Function):
         dk, dla = ctx.saved_tensors
         g = grad_out.to(dk.dtype)
         return g * dk, g * dla, None, None, None, None, None, None, None, None
+
+
+class FoEImplicitLoss(torch.autograd.Function):
+    """The same objective with the paper's own gradient: implicit differentiation at u^T (Sec. 2.5, Eq.
+    implicitdifferentiation and Eq. overallderivative), q = H_E(u^T)^{-1} dL/dw by conjugate gradients on the device.
+
+    loss = FoEImplicitLoss.apply(filters, log_alpha, clean, noisy, iters, lam, gamma, tau, max_cg, cg_tol)
+
+    Exact at a minimiser of the lower-level problem, so `iters` should let the solve converge; tau = 0 takes the
+    certified step of the current filters (the gradient does not depend on tau once u^T is the minimiser)."""
+
+    @staticmethod
+    def forward(ctx, filters, log_alpha, clean, noisy, iters: int, lam: float, gamma: float, tau: float,
+                max_cg: int = 200, cg_tol: float = 1e-5, W: int | None = None):
+        B, H, ld = clean.shape
+        W = W or ld
+        k = filters.detach().float().cpu().numpy()
+        a = np.exp(log_alpha.detach().double().cpu().numpy()).astype(np.float32)
+        handle = F.foe_create(k, a)
+        try:
+            dk = torch.empty((k.shape[0], 49), dtype=torch.float32, device=clean.device)
+            dla = torch.empty((k.shape[0],), dtype=torch.float32, device=clean.device)
+            opts = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_FP32, iters=int(iters), lam=float(lam),
+                               gamma=float(gamma), tau=float(tau))
+            loss, _ = F.foe_train_grad_implicit(handle, clean, noisy, B, H, W, ld, opts, dk, dla, int(max_cg),
+                                                float(cg_tol))
+        finally:
+            F.foe_destroy(handle)
+        ctx.save_for_backward(dk.view(-1, 7, 7).to(filters.device, filters.dtype), dla.to(log_alpha.device, log_alpha.dtype))
+        return torch.tensor(loss, dtype=torch.float64, device=filters.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        dk, dla = ctx.saved_tensors
+        g = grad_out.to(dk.dtype)
+        return g * dk, g * dla, None, None, None, None, None, None, None, None, None
+
+
+def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1e-5, history: int = 10,
+                on_step=None):
+    """Algorithm 1 (Sec. 2.5): L-BFGS over the filters and log-weights of the prior.
+
+    loss_fn(filters, log_alpha) returns the training loss as a differentiable scalar tensor (for instance
+    FoEImplicitLoss.apply or FoEUnrolledLoss.apply with the data bound).  Each iteration is one L-BFGS step with a
+    strong-Wolfe line search; training stops when the relative change of the loss falls below tol, after max_iter
+    iterations, or when a step fails to decrease the loss (the three criteria of the paper's training).
+    on_step(iteration, loss), if given, is called after every step.  Returns (filters, log_alpha, losses, reason),
+    losses[0] being the initial loss."""
+    k = filters.detach().clone().requires_grad_(True)
+    la = log_alpha.detach().clone().requires_grad_(True)
+    # one L-BFGS iteration per step; the line search may take up to 20 evaluations within it
+    opt = torch.optim.LBFGS([k, la], lr=1.0, max_iter=1, max_eval=20, history_size=history,
+                            line_search_fn="strong_wolfe")
+
+    def closure():
+        opt.zero_grad()
+        L = loss_fn(k, la)
+        L.backward()
+        return L
+
+    with torch.no_grad():
+        losses = [float(loss_fn(k, la))]
+    reason = "max_iter"
+    for it in range(max_iter):
+        opt.step(closure)
+        with torch.no_grad():
+            L = float(loss_fn(k, la))
+        prev = losses[-1]
+        losses.append(L)
+        if on_step is not None:
+            on_step(it + 1, L)
+        if not L < prev:
+            reason = "no_decrease"
+            break
+        if abs(prev - L) <= tol * abs(prev):
+            reason = "tol"
+            break
+    return k.detach(), la.detach(), losses, reason

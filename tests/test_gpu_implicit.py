@@ -115,3 +115,19 @@ def test_implicit_rejects_unsupported_options(setup):
     with pytest.raises(F.FoeError) as e:
         F.foe_train_grad_implicit(ctx, cd, cd, 1, 16, 16, 16, opts(5, 0.0, F.FOE_BC_SYMMETRIC), dk, da, max_cg=0)
     assert e.value.status == F.FOE_EINVAL
+
+
+def test_lbfgs_training_with_the_implicit_gradient_decreases_the_loss(setup):
+    # Algorithm 1 on the device: a few L-BFGS iterations over all 48 filters and log-weights on a small batch
+    from paper_1609_05722_gb300.train import FoEImplicitLoss, lbfgs_train
+    k, a, _ = setup
+    H, W, Bn = 32, 32, 2
+    _, _, cd, nd, ld = batch(Bn, H, W, 4.0, 950)
+
+    def loss_fn(kt, lat):
+        return FoEImplicitLoss.apply(kt, lat, cd, nd, 300, 1.0, GAMMA, 0.0, 300, 1e-5, W)
+
+    kt, lat, losses, reason = lbfgs_train(loss_fn, torch.from_numpy(k.astype(np.float64)).view(48, 7, 7),
+                                          torch.from_numpy(np.log(a.astype(np.float64))), max_iter=3, tol=0.0)
+    print(f"L-BFGS (implicit gradient) losses {[round(x, 4) for x in losses]} ({reason})")
+    assert losses[1] < losses[0] and min(losses) < 0.999 * losses[0]
