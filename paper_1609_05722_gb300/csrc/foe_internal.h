@@ -241,7 +241,7 @@ inline foe::StepConsts step_consts(float tau, float gamma, float lambda)
 inline void tile_dims(int prec, int &th, int &tw)
 {
     if (prec == FOE_PREC_BF16 || prec == FOE_PREC_TF32) {
-        th = foe::tc_tile_h();
+        th = foe::tc_tile_h(prec == FOE_PREC_TF32);
         tw = foe::tc_tile_w();
     } else {
         th = tw = foe::f32_tile();

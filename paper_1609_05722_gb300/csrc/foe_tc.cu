@@ -1,9 +1,9 @@
 // Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, kind::f16, or TF32 operands,
 // kind::tf32; FP32 accumulators in tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
 //
-// One CTA owns a 26x26 output tile.  The prior gradient sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF)
-// needs the responses on the tile plus a 3-pixel ring: a 32x32 response region, processed as 8
-// M-tiles of 128 response pixels (4 rows of 32).
+// One CTA owns a 26-wide output tile (46 rows for BF16, 26 for TF32).  The prior gradient
+// sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF) needs the responses on the tile plus a 3-pixel ring: a 32-wide
+// response region of 52 (32) rows, processed as 13 (8) M-tiles of 128 response pixels (4 rows of 32).
 //
 //   forward   R[m][i]  = sum_k A[m][k] Wf[i][k]        M=128, N=48 filters, K=64 (8x8 taps, 49 used)
 //             A is never materialised as an im2col matrix: E holds, for every input position, the 8
@@ -20,7 +20,7 @@
 // TMEM lanes 32(w%4)..32(w%4)+31, i.e. response row 4t+w%4 of M-tile t): warps 0-3 run the expert step,
 // warps 4-7 the col2im.  One thread of warp 8 issues the forward MMAs and one thread of warp 9 the
 // adjoint MMAs, so neither kind of MMA waits behind the other's dependencies.
-// Tensor memory holds two response stages (columns 0 and 64) and two adjoint stages Z(t & 1) (columns
+// Tensor memory holds two response stages (columns 0 and 64) and two adjoint stages Z(g & 1) (columns
 // 128 and 192).  The epilogue writes Psi(t) (packed bf16 pairs, or tf32) over the first columns of R(t)'s
 // stage, and the adjoint MMA reads its A operand from there, so Psi never passes through shared memory;
 // the stage is free again once that MMA is complete, Z(t) once the col2im has loaded it.  Expert and
@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "foe_common.cuh"
 #include "foe_kernels.h"
 
@@ -41,18 +43,40 @@ namespace foe {
 
 namespace {
 
-constexpr int TO = 26;                 // output tile side
-constexpr int RS = TO + 6;             // response region side = 32 = warp width
-constexpr int NMT = RS / 4;            // M-tiles per CTA
-constexpr int EROWS = RS + 7;          // input rows (7 tap rows + 1 zero-weight row)
-constexpr int UR = RS + 7, UC = RS + 8;
+constexpr int TO = 26;                 // output tile width
+constexpr int RS = TO + 6;             // response region width = 32 = warp width
+constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 used)
+
+// Tile height: BF16 tiles are 46 output rows tall (13 M-tiles).  Taller tiles repeat the 3-row response ring
+// less often and amortise each tile's E build, output pass and barriers over more M-tiles; two CTAs still fit an
+// SM because the horizontal col2im sums are kept in FP16 (their magnitude stays far below its range, and its
+// 11-bit significand is finer than the BF16 rounding of u and psi).  TF32 tiles are 26 x 26 with FP32 sums,
+// which keeps their ~4x smaller error.
+template <bool TF>
+struct TcGeo;
+template <>
+struct TcGeo<false> {
+    static constexpr int TOH = 46;
+    using HsT = __half;
+};
+template <>
+struct TcGeo<true> {
+    static constexpr int TOH = 26;
+    using HsT = float;
+};
+template <bool TF>
+constexpr int kRR = TcGeo<TF>::TOH + 6;   // response rows of a tile
+template <bool TF>
+constexpr int kNMT = kRR<TF> / 4;         // M-tiles per tile
+template <bool TF>
+constexpr int kUR = kRR<TF> + 7;          // input rows = E rows (7 tap rows + 1 zero-weight row)
 constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quarter
 constexpr int FWD_WARP = NEPI;         // one thread of this warp issues the forward MMAs
 constexpr int ADJ_WARP = NEPI + 1;     // one thread of this warp issues the adjoint MMAs
 constexpr int NWARP = NEPI + 2;
 constexpr int NTHR = 32 * NWARP;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr uint32_t Z_COL0 = 128;       // R(t) at 64 (t & 1) (48 columns), Z(t) at 128 + 64 (t & 1) (64 columns)
+constexpr uint32_t Z_COL0 = 128;       // R(g) at 64 (g & 1) (48 columns), Z(g) at 128 + 64 (g & 1) (64 columns)
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
@@ -71,11 +95,11 @@ struct TcOps<true> {
 };
 
 // mbarriers
-constexpr int B_FWD = 0;     // [2] forward MMAs of M-tile t complete (t & 1)             count 1 (commit)
+constexpr int B_FWD = 0;     // [2] forward MMAs of M-tile g complete (g & 1)             count 1 (commit)
 constexpr int B_RFREE = 2;   // [2] adjoint MMAs of M-tile t complete: stage t & 1 free  count 1 (commit)
-constexpr int B_PSI = 4;     // [2] Psi(t) written to tensor memory (t & 1)              count 128
-constexpr int B_ADJ = 6;     // [2] adjoint MMAs of M-tile t complete (t & 1)             count 1 (commit)
-constexpr int B_ZFREE = 8;   // [2] Z(t) loaded by every col2im thread (t & 1)           count 128
+constexpr int B_PSI = 4;     // [2] Psi(g) written to tensor memory (g & 1)              count 128
+constexpr int B_ADJ = 6;     // [2] adjoint MMAs of M-tile g complete (g & 1)             count 1 (commit)
+constexpr int B_ZFREE = 8;   // [2] Z(g) loaded by every col2im thread (g & 1)           count 128
 constexpr int B_W = 10;      // filter operand images arrived (bulk copy)                count 1 + tx
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
 constexpr int NBAR = 13;
@@ -87,13 +111,13 @@ constexpr int kNBuf = TF ? 1 : 2;
 
 template <bool TF>
 struct TcSmem {
-    uint4 E[TcOps<TF>::EB][EROWS * RS];   // forward A operand: entry (row, x) holds u(row, x..x+7)
+    uint4 E[TcOps<TF>::EB][kUR<TF> * RS];  // forward A operand: entry (row, x) holds u(row, x..x+7)
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
-    float Hs[7 * RS * RS];      // horizontal col2im partial sums [a][response row][col]
-    float U[kNBuf<TF>][UR * UC];        // fp32 input region (this tile / the next one)
-    float O[kNBuf<TF>][2][TO * TO];     // output-pass operands delta, d (this tile / the next one)
-    int srow[kNBuf<TF>][UR], scol[kNBuf<TF>][UR];  // source row / column of each region row / column (-1: zero)
+    typename TcGeo<TF>::HsT Hs[7 * kRR<TF> * RS];  // horizontal col2im partial sums [a][response row][col]
+    float U[kNBuf<TF>][kUR<TF> * UC];              // fp32 input region (this tile / the next one)
+    float O[kNBuf<TF>][2][TO * TcGeo<TF>::TOH];    // output-pass operands delta, d (this tile / the next one)
+    int srow[kNBuf<TF>][kUR<TF>], scol[kNBuf<TF>][RS + 7];  // source row / column of each region row / column (-1: zero)
     int geo[kNBuf<TF>][4];              // image, oy0, ox0, write limit xe of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
@@ -382,15 +406,20 @@ __device__ __forceinline__ void ipiano_update_f32(float g, float uh, float delta
     ndelta = p - uh;
 }
 
+__device__ __forceinline__ float hs_val(float v) { return v; }
+__device__ __forceinline__ float hs_val(__half v) { return __half2float(v); }
+__device__ __forceinline__ void hs_put(float &d, float v) { d = v; }
+__device__ __forceinline__ void hs_put(__half &d, float v) { d = __float2half_rn(v); }
+
 // Sum over the 7 tap rows of the horizontal partials at (qy, qx) of the response region.  Unchecked:
-// for an output position (qy, qx in 3..28) every row qy - a + 3 lies in the region.
+// for an output position (qy in 3..TOH+2, qx in 3..28) every row qy - a + 3 lies in the region.
 template <bool TF>
 __device__ __forceinline__ float hs_sum(const TcSmem<TF> &S, int qy, int qx)
 {
-    const float *p = &S.Hs[(qy + 3) * RS + qx];
+    const auto *p = &S.Hs[(qy + 3) * RS + qx];
     float g = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 7; ++a) g += p[a * (RS * RS - RS)];
+    for (int a = 0; a < 7; ++a) g += hs_val(p[a * (kRR<TF> * RS - RS)]);
     return g;
 }
 
@@ -404,7 +433,7 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
         const int r = qy - a + 3;
-        if (r >= 0 && r < RS) g += S.Hs[(a * RS + r) * RS + qx];
+        if (r >= 0 && r < kRR<TF>) g += hs_val(S.Hs[(a * kRR<TF> + r) * RS + qx]);
     }
     return g;
 }
@@ -416,13 +445,14 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
 // and the tile before it writes only the columns left of that origin.  Rows need no such rule: the vertical part
 // of the col2im reads response rows, and the rows that a reflection asks for that lie in the image are always
 // within 3 rows of the output row.
+template <bool TF>
 __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0, int &xe)
 {
     im = tile_image(A, tile);
     const ImgDesc &D = A.img[im];
     const int lt = tile - A.tile_prefix[im];
     const int tx = lt % D.tiles_x;
-    oy0 = (lt / D.tiles_x) * TO;
+    oy0 = (lt / D.tiles_x) * TcGeo<TF>::TOH;
     ox0 = tx * TO;
     xe = min(ox0 + TO, D.W);
     if (D.W > TO) {
@@ -438,20 +468,21 @@ template <int MODE, bool TF>
 __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
                                            int lane)
 {
-    if (tid == 0) tile_geometry(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
+    if (tid == 0) tile_geometry<TF>(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
     __syncthreads();
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
     const int H = D.H, W = D.W, ld = D.ld;
+    constexpr int UR = kUR<TF>, UCU = RS + 7;  // input rows, input columns used
     if (tid < UR) S.srow[b][tid] = pad_index(oy0 - 6 + tid, H, A.bc);
-    else if (tid < 2 * UR) S.scol[b][tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
+    else if (tid < UR + UCU) S.scol[b][tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
     __syncthreads();
     const float *uin = D.u_hi[A.parity];
     float *U = S.U[b];
     for (int r = warp; r < UR; r += NWARP) {
         const int sy = S.srow[b][r];
         const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
-        for (int c = lane; c < UR; c += 32) {
+        for (int c = lane; c < UCU; c += 32) {
             const int sx = S.scol[b][c];
             if (sy < 0 || sx < 0) U[r * UC + c] = 0.0f;
             else cp_async4(&U[r * UC + c], src + sx);
@@ -459,7 +490,7 @@ __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, i
     }
     if (lane < TO) {
         const int gx = ox0 + lane;
-        for (int r = warp; r < TO; r += NWARP) {
+        for (int r = warp; r < TcGeo<TF>::TOH; r += NWARP) {
             const int gy = oy0 + r, j = r * TO + lane;
             if (gy >= H || gx >= W) continue;
             const size_t idx = (size_t)gy * ld + gx;
@@ -543,7 +574,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int sidx = lane + 32 * h;
-                v += Ub[(2 + 5 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
+                v += Ub[(2 + (kUR<TF> - 4) / 7 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
             }
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) S.red[0] = v * (1.0f / 64.0f);
@@ -552,7 +583,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         const float mean = S.red[0];
         // one thread per 4 consecutive entries of an E row: the 11 inputs they span are loaded (three 16-byte
         // loads), shifted and rounded once
-        for (int item = tid; item < EROWS * (RS / 4); item += NTHR) {
+        for (int item = tid; item < kUR<TF> * (RS / 4); item += NTHR) {
             const int i = item / (RS / 4), x0 = 4 * (item % (RS / 4));
             const float4 *src = reinterpret_cast<const float4 *>(&Ub[i * UC + x0]);
             const float4 a0 = src[0], a1 = src[1], a2 = src[2];
@@ -585,19 +616,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (warp == FWD_WARP || warp == ADJ_WARP) {
             {
                 // ---------------- MMA issue (warp-uniform; one elected lane issues) ----------------
-                // stage barriers complete four times per tile, so their phase parities repeat every tile; the waits
-                // for M-tile t - 2 reach back into the previous tile for t < 2 (g counts M-tiles over all tiles)
+                // g counts M-tiles over all tiles of the CTA: M-tile g uses stage g & 1, and a stage barrier's phase
+                // for M-tile g has parity (g >> 1) & 1 (a tile may hold an odd number of M-tiles)
                 bool ok = k > 0 || mbar_wait_warp(&S.bar[B_W], 0, abort_flag, status);
                 if (warp == FWD_WARP) {
                     // R(t) = E-window(t) x Wf^T into stage t & 1, once the adjoint of M-tile t - 2 is complete
                     constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
                     const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
                     const uint64_t dE = sdesc(e0, TF ? e1 - e0 : RS * 16, 128), dW = sdesc(smem_u32(S.Wf), 768, 128);
-                    for (int t = 0; ok && t < NMT; ++t) {
-                        const int g = NMT * k + t;
-                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_RFREE + (t & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
+                    for (int t = 0; ok && t < kNMT<TF>; ++t) {
+                        const int g = kNMT<TF> * k + t;
+                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_RFREE + (g & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
                         fence_after();
-                        const uint32_t d = tmem + 64 * (t & 1);
+                        const uint32_t d = tmem + 64 * (g & 1);
                         if (TF) {
                             // K-step a = one tap row (8 columns: E[0] holds columns 0-3, E[1] columns 4-7); row 7 has
                             // zero weights and is skipped
@@ -609,7 +640,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                             for (int kk = 0; kk < 4; ++kk)
                                 mma_elect<TF>(d, dE + (uint64_t)((4 * t + 2 * kk) * RS), dW + (uint64_t)(kk * 96), IDF, kk > 0);
                         }
-                        commit_elect(&S.bar[B_FWD + (t & 1)]);
+                        commit_elect(&S.bar[B_FWD + (g & 1)]);
                     }
                 } else {
                     // Z(t) = Psi(t) x Wa^T into Z stage t & 1, once Psi(t) is in tensor memory and Z(t - 2) has
@@ -617,17 +648,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     // or 8 tf32 filters)
                     constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
                     const uint64_t dWa = sdesc(smem_u32(S.Wa), 1024, 128);
-                    for (int t = 0; ok && t < NMT; ++t) {
-                        if (!mbar_wait_warp(&S.bar[B_PSI + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
-                        const int g = NMT * k + t;
-                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_ZFREE + (t & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
+                    for (int t = 0; ok && t < kNMT<TF>; ++t) {
+                        const int g = kNMT<TF> * k + t;
+                        if (!mbar_wait_warp(&S.bar[B_PSI + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
+                        if (g >= 2 && !mbar_wait_warp(&S.bar[B_ZFREE + (g & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
                         fence_after();
-                        const uint32_t d = tmem + Z_COL0 + 64 * (t & 1), a = tmem + 64 * (t & 1);
+                        const uint32_t d = tmem + Z_COL0 + 64 * (g & 1), a = tmem + 64 * (g & 1);
 #pragma unroll
                         for (int kk = 0; kk < (TF ? 6 : 3); ++kk)
                             mma_ta_elect<TF>(d, a + 8 * kk, dWa + (uint64_t)(kk * 128), IDA, kk > 0);
-                        commit_elect(&S.bar[B_ADJ + (t & 1)]);
-                        commit_elect(&S.bar[B_RFREE + (t & 1)]);
+                        commit_elect(&S.bar[B_ADJ + (g & 1)]);
+                        commit_elect(&S.bar[B_RFREE + (g & 1)]);
                     }
                 }
             }
@@ -640,14 +671,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             const int q = warp & 3;
             // interior tile: the whole response region lies in the image, so no response is masked and no
             // lane outside 3..28 is ever read (no padding fold)
-            const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + RS - 3 <= H && ox0 + RS - 3 <= W;
+            const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + kRR<TF> - 3 <= H && ox0 + RS - 3 <= W;
             const uint32_t lane_base = (uint32_t)(32 * q) << 16;
             if (warp < 4) {
                 const int gx = ox0 - 3 + lane;
-                for (int t = 0; t < NMT; ++t) {
-                    if (!mbar_wait(&S.bar[B_FWD + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                for (int t = 0; t < kNMT<TF>; ++t) {
+                    const int g = kNMT<TF> * k + t;
+                    if (!mbar_wait(&S.bar[B_FWD + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                     fence_after();
-                    const uint32_t rc = tmem + lane_base + 64 * (t & 1);
+                    const uint32_t rc = tmem + lane_base + 64 * (g & 1);
                     const int gy = oy0 - 3 + 4 * t + q;
                     const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
                     if (TF) {
@@ -684,20 +716,21 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     }
                     tmem_wait_st();
                     fence_before();
-                    mbar_arrive(&S.bar[B_PSI + (t & 1)]);
+                    mbar_arrive(&S.bar[B_PSI + (g & 1)]);
                 }
             } else {
-                for (int t = 0; t < NMT; ++t) {
-                    if (!mbar_wait(&S.bar[B_ADJ + (t & 1)], (t >> 1) & 1, abort_flag, status)) break;
+                for (int t = 0; t < kNMT<TF>; ++t) {
+                    const int g = kNMT<TF> * k + t;
+                    if (!mbar_wait(&S.bar[B_ADJ + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                     fence_after();
                     float z[56];
-                    const uint32_t zc = tmem + lane_base + Z_COL0 + 64 * (t & 1);
+                    const uint32_t zc = tmem + lane_base + Z_COL0 + 64 * (g & 1);
                     tmem_ld32(zc, z);
                     tmem_ld16(zc + 32, z + 32);
                     tmem_ld8(zc + 48, z + 48);  // tap row 7 has zero weights
                     tmem_wait_ld();
                     fence_before();
-                    mbar_arrive(&S.bar[B_ZFREE + (t & 1)]);
+                    mbar_arrive(&S.bar[B_ZFREE + (g & 1)]);
                     const int rr = 4 * t + q;
                     if (interior) {
                         // all 42 shuffles first, then the sums: independent work to cover the shuffle latency
@@ -713,8 +746,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                         }
 #pragma unroll
                         for (int a = 0; a < 7; ++a)
-                            S.Hs[(a * RS + rr) * RS + lane] =
-                                ((z[8 * a + 3] + sh[a][0]) + (sh[a][1] + sh[a][2])) + ((sh[a][3] + sh[a][4]) + sh[a][5]);
+                            hs_put(S.Hs[(a * kRR<TF> + rr) * RS + lane],
+                                   ((z[8 * a + 3] + sh[a][0]) + (sh[a][1] + sh[a][2])) + ((sh[a][3] + sh[a][4]) + sh[a][5]));
                     } else {
 #pragma unroll
                         for (int a = 0; a < 7; ++a) {
@@ -728,7 +761,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                                 const float v = __shfl_sync(0xffffffffu, za[bb], src & 31);
                                 h += (src >= 0 && src < 32) ? v : 0.0f;
                             }
-                            S.Hs[(a * RS + rr) * RS + lane] = h;
+                            hs_put(S.Hs[(a * kRR<TF> + rr) * RS + lane], h);
                         }
                     }
                 }
@@ -741,8 +774,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
         // warp w handles output rows w, w + 9/10, w + 2*(9/10) (lane = column): the rows are unrolled so that their
         // independent update chains interleave
-        const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TO > H - 3 || ox0 + TO > W - 3);
-        constexpr int NR = (TO + NWARP - 1) / NWARP;
+        constexpr int TOH = TcGeo<TF>::TOH;
+        const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TOH > H - 3 || ox0 + TO > W - 3);
+        constexpr int NR = (TOH + NWARP - 1) / NWARP;
         if (lane < TO) {
             const int xo = 3 + lane, gx = ox0 + lane;
             float g[NR], uh[NR];
@@ -750,7 +784,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 const int r = warp + k2 * NWARP, yo = 3 + r, gy = oy0 + r;
-                ok_r[k2] = r < TO && gy < H && gx < xe;
+                ok_r[k2] = r < TOH && gy < H && gx < xe;
                 g[k2] = 0.0f;
                 uh[k2] = 0.0f;
                 if (ok_r[k2]) {
@@ -818,7 +852,7 @@ constexpr size_t smem_request()
 
 }  // namespace
 
-int tc_tile_h() { return TO; }
+int tc_tile_h(bool tf32) { return tf32 ? TcGeo<true>::TOH : TcGeo<false>::TOH; }
 int tc_tile_w() { return TO; }
 size_t tc_smem_bytes() { return smem_request<false>(); }
 
