@@ -1,9 +1,9 @@
 // Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, kind::f16, or TF32 operands,
 // kind::tf32; FP32 accumulators in tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
 //
-// One CTA owns a 26-wide output tile (46 rows for BF16, 26 for TF32).  The prior gradient
+// One CTA owns a 26-wide output tile (58 rows for BF16, 26 for TF32).  The prior gradient
 // sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF) needs the responses on the tile plus a 3-pixel ring: a 32-wide
-// response region of 52 (32) rows, processed as 13 (8) M-tiles of 128 response pixels (4 rows of 32).
+// response region of 64 (32) rows, processed as 16 (8) M-tiles of 128 response pixels (4 rows of 32).
 //
 //   forward   R[m][i]  = sum_k A[m][k] Wf[i][k]        M=128, N=48 filters, K=64 (8x8 taps, 49 used)
 //             A is never materialised as an im2col matrix: E holds, for every input position, the 8
@@ -47,7 +47,7 @@ constexpr int TO = 26;                 // output tile width
 constexpr int RS = TO + 6;             // response region width = 32 = warp width
 constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 used)
 
-// Tile height: BF16 tiles are 46 output rows tall (13 M-tiles).  Taller tiles repeat the 3-row response ring
+// Tile height: BF16 tiles are 58 output rows tall (16 M-tiles).  Taller tiles repeat the 3-row response ring
 // less often and amortise each tile's E build, output pass and barriers over more M-tiles; two CTAs still fit an
 // SM because the horizontal col2im sums are kept in FP16 (their magnitude stays far below its range, and its
 // 11-bit significand is finer than the BF16 rounding of u and psi).  TF32 tiles are 26 x 26 with FP32 sums,
@@ -56,7 +56,7 @@ template <bool TF>
 struct TcGeo;
 template <>
 struct TcGeo<false> {
-    static constexpr int TOH = 46;
+    static constexpr int TOH = 58;
     using HsT = __half;
 };
 template <>
@@ -104,8 +104,8 @@ constexpr int B_W = 10;      // filter operand images arrived (bulk copy)       
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
 constexpr int NBAR = 13;
 
-// Input-region / output-operand buffers: two for BF16 (the next tile is copied in during the current one), one
-// for TF32 (whose larger operand images leave room for only one if two CTAs are to share an SM).
+// Input-region buffers: two for BF16 (the next tile is copied in during the current one), one for TF32 (whose
+// larger operand images leave room for only one if two CTAs are to share an SM).
 template <bool TF>
 constexpr int kNBuf = TF ? 1 : 2;
 
@@ -116,7 +116,7 @@ struct TcSmem {
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
     typename TcGeo<TF>::HsT Hs[7 * kRR<TF> * RS];  // horizontal col2im partial sums [a][response row][col]
     float U[kNBuf<TF>][kUR<TF> * UC];              // fp32 input region (this tile / the next one)
-    float O[kNBuf<TF>][2][TO * TcGeo<TF>::TOH];    // output-pass operands delta, d (this tile / the next one)
+    float O[2][TO * TcGeo<TF>::TOH];               // output-pass operands delta, d (staged after the previous tile)
     int srow[kNBuf<TF>][kUR<TF>], scol[kNBuf<TF>][RS + 7];  // source row / column of each region row / column (-1: zero)
     int geo[kNBuf<TF>][4];              // image, oy0, ox0, write limit xe of the tile in buffer b
     uint64_t bar[NBAR];
@@ -124,6 +124,9 @@ struct TcSmem {
     int abort_flag;
     float red[NWARP];
 };
+// Two CTAs share an SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+static_assert(sizeof(TcSmem<false>) + 1024 <= 228 * 1024 / 2, "BF16 tile kernel: two CTAs per SM");
+static_assert(sizeof(TcSmem<true>) + 1024 <= 228 * 1024 / 2, "TF32 tile kernel: two CTAs per SM");
 // Wf and Wa are filled by one bulk copy of the packed operand images
 static_assert(offsetof(TcSmem<false>, Wa) == offsetof(TcSmem<false>, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
 static_assert(offsetof(TcSmem<true>, Wa) == offsetof(TcSmem<true>, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
@@ -462,11 +465,12 @@ __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int
     }
 }
 
-// Issue the asynchronous copies of a tile's input region and output-pass operands into buffer b (all threads;
-// one cp.async group).  Positions outside the padded image are zero-filled with plain stores.
-template <int MODE, bool TF>
-__device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
-                                           int lane)
+// Issue the asynchronous copies of a tile's input region into buffer b and record its geometry there (all
+// threads; the caller commits the cp.async group).  Positions outside the padded image are zero-filled with plain
+// stores.
+template <bool TF>
+__device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
+                                            int lane)
 {
     if (tid == 0) tile_geometry<TF>(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
     __syncthreads();
@@ -488,17 +492,27 @@ __device__ __forceinline__ void stage_tile(const LaunchArgs &A, TcSmem<TF> &S, i
             else cp_async4(&U[r * UC + c], src + sx);
         }
     }
+}
+
+// Issue the asynchronous copies of the output-pass operands (delta, d) of the tile whose geometry is in buffer b
+// (all threads; the caller commits).  The operand buffer is single: these are issued once the previous tile's
+// output pass is over, and are first needed at the end of the tile's own pipeline.
+template <int MODE, bool TF>
+__device__ __forceinline__ void stage_operands(const LaunchArgs &A, TcSmem<TF> &S, int b, int warp, int lane)
+{
+    const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
+    const ImgDesc &D = A.img[im];
+    const int H = D.H, W = D.W, ld = D.ld;
     if (lane < TO) {
         const int gx = ox0 + lane;
         for (int r = warp; r < TcGeo<TF>::TOH; r += NWARP) {
             const int gy = oy0 + r, j = r * TO + lane;
             if (gy >= H || gx >= W) continue;
             const size_t idx = (size_t)gy * ld + gx;
-            if (MODE == kStep) cp_async4(&S.O[b][0][j], D.delta + idx);
-            cp_async4(&S.O[b][1][j], D.d + idx);
+            if (MODE == kStep) cp_async4(&S.O[0][j], D.delta + idx);
+            cp_async4(&S.O[1][j], D.d + idx);
         }
     }
-    cp_async_commit();
 }
 
 // Persistent: CTA c processes tiles c, c + gridDim.x, ...; tensor memory, barriers and the filter operands
@@ -543,7 +557,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
         bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
     }
-    stage_tile<MODE, TF>(A, S, blockIdx.x, 0, tid, warp, lane);
+    stage_input<TF>(A, S, blockIdx.x, 0, tid, warp, lane);
+    stage_operands<MODE, TF>(A, S, 0, warp, lane);
+    cp_async_commit();
     fence_before();
     __syncthreads();
     fence_after();
@@ -558,12 +574,16 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         const ImgDesc &D = A.img[im];
         const int H = D.H, W = D.W, ld = D.ld;
 
-        // this tile's copies (issued during the previous tile, or after it with one buffer) have landed; with two
-        // buffers, start the next tile's
-        cp_async_wait<0>();
+        // this tile's input region has landed (with two buffers it was copied during the previous tile, and the
+        // newest group, this tile's output-pass operands, may still be in flight); with two buffers, start the next
+        // tile's.  Groups are committed even when empty, so their count per tile is fixed.
+        if (NB == 2 && k > 0) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncthreads();
-        if (NB == 2 && tile + (int)gridDim.x < ntiles)
-            stage_tile<MODE, TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+        if (NB == 2) {
+            if (tile + (int)gridDim.x < ntiles) stage_input<TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+            cp_async_commit();
+        }
 
         // ---- operand offset (BF16 range), then E ----
         // Any constant c gives K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the
@@ -768,6 +788,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             }
         }
 
+        // the output-pass operands have landed (only the next tile's input region may still be in flight)
+        if (NB == 2) cp_async_wait<1>();
         fence_before();
         __syncthreads();
 
@@ -805,10 +827,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 const int r = warp + k2 * NWARP, j = r * TO + lane;
                 const size_t idx = (size_t)(oy0 + r) * ld + gx;
                 if (MODE == kGrad) {
-                    D.out[idx] = g[k2] + data_grad(uh[k2], S.O[buf][1][j], D.model, D.sc.lambda);
+                    D.out[idx] = g[k2] + data_grad(uh[k2], S.O[1][j], D.model, D.sc.lambda);
                 } else {
                     float nh, nd;
-                    ipiano_update_f32(g[k2], uh[k2], S.O[buf][0][j], S.O[buf][1][j], D.model, D.sc, nh, nd);
+                    ipiano_update_f32(g[k2], uh[k2], S.O[0][j], S.O[1][j], D.model, D.sc, nh, nd);
                     D.u_hi[A.parity ^ 1][idx] = nh;
                     D.delta[idx] = nd;
                 }
@@ -818,8 +840,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
-        if (NB == 1 && tile + (int)gridDim.x < ntiles)
-            stage_tile<MODE, TF>(A, S, tile + gridDim.x, 0, tid, warp, lane);
+        if (NB == 1) {
+            if (tile + (int)gridDim.x < ntiles) {
+                stage_input<TF>(A, S, tile + gridDim.x, 0, tid, warp, lane);
+                stage_operands<MODE, TF>(A, S, 0, warp, lane);
+            }
+        } else if (tile + (int)gridDim.x < ntiles) {
+            stage_operands<MODE, TF>(A, S, buf ^ 1, warp, lane);
+        }
+        cp_async_commit();
     }
 
     // every MMA issued by the two MMA threads is complete before tensor memory is released
