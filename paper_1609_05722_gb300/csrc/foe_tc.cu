@@ -104,21 +104,16 @@ constexpr int B_W = 10;      // filter operand images arrived (bulk copy)       
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
 constexpr int NBAR = 13;
 
-// Input-region buffers: two for BF16 (the next tile is copied in during the current one), one for TF32 (whose
-// larger operand images leave room for only one if two CTAs are to share an SM).
-template <bool TF>
-constexpr int kNBuf = TF ? 1 : 2;
-
 template <bool TF>
 struct TcSmem {
     uint4 E[TcOps<TF>::EB][kUR<TF> * RS];  // forward A operand: entry (row, x) holds u(row, x..x+7)
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
     typename TcGeo<TF>::HsT Hs[7 * kRR<TF> * RS];  // horizontal col2im partial sums [a][response row][col]
-    float U[kNBuf<TF>][kUR<TF> * UC];              // fp32 input region (this tile / the next one)
+    float U[2][kUR<TF> * UC];                      // fp32 input region (this tile / the next one, copied in meanwhile)
     float O[2][TO * TcGeo<TF>::TOH];               // output-pass operands delta, d (staged after the previous tile)
-    int srow[kNBuf<TF>][kUR<TF>], scol[kNBuf<TF>][RS + 7];  // source row / column of each region row / column (-1: zero)
-    int geo[kNBuf<TF>][4];              // image, oy0, ox0, write limit xe of the tile in buffer b
+    int srow[2][kUR<TF>], scol[2][RS + 7];         // source row / column of each region row / column (-1: zero)
+    int geo[2][4];                                 // image, oy0, ox0, write limit xe of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -568,22 +563,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        constexpr int NB = kNBuf<TF>;
-        const int buf = NB == 2 ? (k & 1) : 0;
+        const int buf = k & 1;
         const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3];
         const ImgDesc &D = A.img[im];
         const int H = D.H, W = D.W, ld = D.ld;
 
-        // this tile's input region has landed (with two buffers it was copied during the previous tile, and the
-        // newest group, this tile's output-pass operands, may still be in flight); with two buffers, start the next
-        // tile's.  Groups are committed even when empty, so their count per tile is fixed.
-        if (NB == 2 && k > 0) cp_async_wait<1>();
+        // this tile's input region has landed (it was copied in during the previous tile; the newest group, this
+        // tile's output-pass operands, may still be in flight); start the next tile's.  Groups are committed even
+        // when empty, so their count per tile is fixed.
+        if (k > 0) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();
-        if (NB == 2) {
-            if (tile + (int)gridDim.x < ntiles) stage_input<TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
-            cp_async_commit();
-        }
+        if (tile + (int)gridDim.x < ntiles) stage_input<TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+        cp_async_commit();
 
         // ---- operand offset (BF16 range), then E ----
         // Any constant c gives K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the
@@ -789,7 +781,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         }
 
         // the output-pass operands have landed (only the next tile's input region may still be in flight)
-        if (NB == 2) cp_async_wait<1>();
+        cp_async_wait<1>();
         fence_before();
         __syncthreads();
 
@@ -840,14 +832,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
-        if (NB == 1) {
-            if (tile + (int)gridDim.x < ntiles) {
-                stage_input<TF>(A, S, tile + gridDim.x, 0, tid, warp, lane);
-                stage_operands<MODE, TF>(A, S, 0, warp, lane);
-            }
-        } else if (tile + (int)gridDim.x < ntiles) {
-            stage_operands<MODE, TF>(A, S, buf ^ 1, warp, lane);
-        }
+        if (tile + (int)gridDim.x < ntiles) stage_operands<MODE, TF>(A, S, buf ^ 1, warp, lane);
         cp_async_commit();
     }
 
