@@ -37,6 +37,7 @@ struct ImgDesc {
     float *out;                // kGrad: gradient; unused otherwise
     int H, W, ld;
     int tiles_x;
+    int tile_h;                // tensor-core path: output rows of this image's tiles
     int model;
     StepConsts sc;
 };

@@ -14,7 +14,7 @@ cudaError_t f32_setup();
 cudaError_t f32_launch(const LaunchArgs &a, int mode, cudaStream_t s);
 
 // Tensor-core (tcgen05, BF16 or TF32) fused tile kernel (foe_tc.cu).
-int tc_tile_h(bool tf32);  // output rows of a tensor-core tile (its width is tc_tile_w())
+int tc_tile_h(bool tf32, int H);  // output rows of the tensor-core tiles of an image of H rows (width: tc_tile_w())
 int tc_tile_w();
 size_t tc_smem_bytes();
 cudaError_t tc_setup();

@@ -1,9 +1,9 @@
 // Tensor-core fused FoE tile kernel for sm_103a: tcgen05.mma (BF16 operands, kind::f16, or TF32 operands,
 // kind::tf32; FP32 accumulators in tensor memory), one iPiano step (Eq. iPianoupdate) per launch.
 //
-// One CTA owns a 26-wide output tile (58 rows for BF16, 26 for TF32).  The prior gradient
-// sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF) needs the responses on the tile plus a 3-pixel ring: a 32-wide
-// response region of 64 (32) rows, processed as 16 (8) M-tiles of 128 response pixels (4 rows of 32).
+// One CTA owns a 26-wide output tile of 58 or 26 rows (below).  The prior gradient sum_i alpha_i K_i^T rho'(K_i u)
+// (Eq. FoEF) needs the responses on the tile plus a 3-pixel ring: a 32-wide response region of 64 (32) rows,
+// processed as 16 (8) M-tiles of 128 response pixels (4 rows of 32).
 //
 //   forward   R[m][i]  = sum_k A[m][k] Wf[i][k]        M=128, N=48 filters, K=64 (8x8 taps, 49 used)
 //             A is never materialised as an im2col matrix: E holds, for every input position, the 8
@@ -47,29 +47,29 @@ constexpr int TO = 26;                 // output tile width
 constexpr int RS = TO + 6;             // response region width = 32 = warp width
 constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 used)
 
-// Tile height: BF16 tiles are 58 output rows tall (16 M-tiles).  Taller tiles repeat the 3-row response ring
-// less often and amortise each tile's E build, output pass and barriers over more M-tiles; two CTAs still fit an
-// SM because the horizontal col2im sums are kept in FP16 (their magnitude stays far below its range, and its
-// 11-bit significand is finer than the BF16 rounding of u and psi).  TF32 tiles are 26 x 26 with FP32 sums,
-// which keeps their ~4x smaller error.
+// Tile height (per image, chosen by the host): BF16 images of at least 232 rows use 26 x 58 tiles (16 M-tiles),
+// which repeat the 3-row response ring less often and amortise each tile's E build, output pass and barriers over
+// more M-tiles; smaller images, and the TF32 path, use 26 x 26 tiles, which keep more SMs busy on small work.  The
+// height is a template parameter of the kernel, and a launch whose images use both heights runs as two kernel
+// launches, one per height.  An image is tiled the same way whatever else shares its launch, so its result does not
+// depend on the batch.  Two CTAs still fit an SM with the tall tiles because the horizontal col2im sums are kept in
+// FP16 on the BF16 path (their magnitude stays far below its range, and its 11-bit significand is finer than the
+// BF16 rounding of u and psi); TF32 keeps FP32 sums and its ~4x smaller error.
+constexpr int kTallH = 58, kShortH = 26;
 template <bool TF>
-struct TcGeo;
-template <>
-struct TcGeo<false> {
-    static constexpr int TOH = 58;
-    using HsT = __half;
+struct HsType {
+    using T = __half;
 };
 template <>
-struct TcGeo<true> {
-    static constexpr int TOH = 26;
-    using HsT = float;
+struct HsType<true> {
+    using T = float;
 };
-template <bool TF>
-constexpr int kRR = TcGeo<TF>::TOH + 6;   // response rows of a tile
-template <bool TF>
-constexpr int kNMT = kRR<TF> / 4;         // M-tiles per tile
-template <bool TF>
-constexpr int kUR = kRR<TF> + 7;          // input rows = E rows (7 tap rows + 1 zero-weight row)
+template <int TOH>
+constexpr int kRR = TOH + 6;              // response rows of a tile
+template <int TOH>
+constexpr int kNMT = kRR<TOH> / 4;        // M-tiles per tile
+template <int TOH>
+constexpr int kUR = kRR<TOH> + 7;         // input rows = E rows (7 tap rows + 1 zero-weight row)
 constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quarter
 constexpr int FWD_WARP = NEPI;         // one thread of this warp issues the forward MMAs
 constexpr int ADJ_WARP = NEPI + 1;     // one thread of this warp issues the adjoint MMAs
@@ -104,15 +104,15 @@ constexpr int B_W = 10;      // filter operand images arrived (bulk copy)       
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
 constexpr int NBAR = 13;
 
-template <bool TF>
+template <bool TF, int TOH>
 struct TcSmem {
-    uint4 E[TcOps<TF>::EB][kUR<TF> * RS];  // forward A operand: entry (row, x) holds u(row, x..x+7)
+    uint4 E[TcOps<TF>::EB][kUR<TOH> * RS];  // forward A operand: entry (row, x) holds u(row, x..x+7)
     uint4 Wf[TcOps<TF>::WF];               // forward B operand [tap row a][(chunk)][filter][tap cols]
     uint4 Wa[TcOps<TF>::WA];               // adjoint B operand [filter chunk][tap 8a+b][filters in chunk]
-    typename TcGeo<TF>::HsT Hs[7 * kRR<TF> * RS];  // horizontal col2im partial sums [a][response row][col]
-    float U[2][kUR<TF> * UC];                      // fp32 input region (this tile / the next one, copied in meanwhile)
-    float O[2][TO * TcGeo<TF>::TOH];               // output-pass operands delta, d (staged after the previous tile)
-    int srow[2][kUR<TF>], scol[2][RS + 7];         // source row / column of each region row / column (-1: zero)
+    typename HsType<TF>::T Hs[7 * kRR<TOH> * RS];  // horizontal col2im partial sums [a][response row][col]
+    float U[2][kUR<TOH> * UC];                     // fp32 input region (this tile / the next one, copied in meanwhile)
+    float O[2][TO * TOH];                          // output-pass operands delta, d (staged after the previous tile)
+    int srow[2][kUR<TOH>], scol[2][RS + 7];        // source row / column of each region row / column (-1: zero)
     int geo[2][4];                                 // image, oy0, ox0, write limit xe of the tile in buffer b
     uint64_t bar[NBAR];
     uint32_t tmem_base;
@@ -120,11 +120,16 @@ struct TcSmem {
     float red[NWARP];
 };
 // Two CTAs share an SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-static_assert(sizeof(TcSmem<false>) + 1024 <= 228 * 1024 / 2, "BF16 tile kernel: two CTAs per SM");
-static_assert(sizeof(TcSmem<true>) + 1024 <= 228 * 1024 / 2, "TF32 tile kernel: two CTAs per SM");
+static_assert(sizeof(TcSmem<false, kTallH>) + 1024 <= 228 * 1024 / 2, "BF16 tall tiles: two CTAs per SM");
+static_assert(sizeof(TcSmem<false, kShortH>) + 1024 <= 228 * 1024 / 2, "BF16 tiles: two CTAs per SM");
+static_assert(sizeof(TcSmem<true, kShortH>) + 1024 <= 228 * 1024 / 2, "TF32 tiles: two CTAs per SM");
 // Wf and Wa are filled by one bulk copy of the packed operand images
-static_assert(offsetof(TcSmem<false>, Wa) == offsetof(TcSmem<false>, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
-static_assert(offsetof(TcSmem<true>, Wa) == offsetof(TcSmem<true>, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
+using SmemBf16Tall = TcSmem<false, kTallH>;
+using SmemBf16 = TcSmem<false, kShortH>;
+using SmemTf32 = TcSmem<true, kShortH>;
+static_assert(offsetof(SmemBf16Tall, Wa) == offsetof(SmemBf16Tall, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
+static_assert(offsetof(SmemBf16, Wa) == offsetof(SmemBf16, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
+static_assert(offsetof(SmemTf32, Wa) == offsetof(SmemTf32, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -411,27 +416,27 @@ __device__ __forceinline__ void hs_put(__half &d, float v) { d = __float2half_rn
 
 // Sum over the 7 tap rows of the horizontal partials at (qy, qx) of the response region.  Unchecked:
 // for an output position (qy in 3..TOH+2, qx in 3..28) every row qy - a + 3 lies in the region.
-template <bool TF>
-__device__ __forceinline__ float hs_sum(const TcSmem<TF> &S, int qy, int qx)
+template <bool TF, int TOH>
+__device__ __forceinline__ float hs_sum(const TcSmem<TF, TOH> &S, int qy, int qx)
 {
     const auto *p = &S.Hs[(qy + 3) * RS + qx];
     float g = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 7; ++a) g += hs_val(p[a * (kRR<TF> * RS - RS)]);
+    for (int a = 0; a < 7; ++a) g += hs_val(p[a * (kRR<TOH> * RS - RS)]);
     return g;
 }
 
 // The same at an arbitrary region position (padding fold); rows and columns outside the region are
 // outside the image whenever they are asked for, so they add 0.
-template <bool TF>
-__device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
+template <bool TF, int TOH>
+__device__ __forceinline__ float hs_gather(const TcSmem<TF, TOH> &S, int qy, int qx)
 {
     if (qx < 0 || qx >= RS) return 0.0f;
     float g = 0.0f;
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
         const int r = qy - a + 3;
-        if (r >= 0 && r < kRR<TF>) g += hs_val(S.Hs[(a * kRR<TF> + r) * RS + qx]);
+        if (r >= 0 && r < kRR<TOH>) g += hs_val(S.Hs[(a * kRR<TOH> + r) * RS + qx]);
     }
     return g;
 }
@@ -443,14 +448,14 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF> &S, int qy, int qx)
 // and the tile before it writes only the columns left of that origin.  Rows need no such rule: the vertical part
 // of the col2im reads response rows, and the rows that a reflection asks for that lie in the image are always
 // within 3 rows of the output row.
-template <bool TF>
+template <int TOH>
 __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0, int &xe)
 {
     im = tile_image(A, tile);
     const ImgDesc &D = A.img[im];
     const int lt = tile - A.tile_prefix[im];
     const int tx = lt % D.tiles_x;
-    oy0 = (lt / D.tiles_x) * TcGeo<TF>::TOH;
+    oy0 = (lt / D.tiles_x) * TOH;
     ox0 = tx * TO;
     xe = min(ox0 + TO, D.W);
     if (D.W > TO) {
@@ -463,16 +468,16 @@ __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int
 // Issue the asynchronous copies of a tile's input region into buffer b and record its geometry there (all
 // threads; the caller commits the cp.async group).  Positions outside the padded image are zero-filled with plain
 // stores.
-template <bool TF>
-__device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF> &S, int tile, int b, int tid, int warp,
+template <bool TF, int TOH>
+__device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH> &S, int tile, int b, int tid, int warp,
                                             int lane)
 {
-    if (tid == 0) tile_geometry<TF>(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
+    if (tid == 0) tile_geometry<TOH>(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
     __syncthreads();
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
     const int H = D.H, W = D.W, ld = D.ld;
-    constexpr int UR = kUR<TF>, UCU = RS + 7;  // input rows, input columns used
+    constexpr int UR = kUR<TOH>, UCU = RS + 7;  // input rows, input columns used
     if (tid < UR) S.srow[b][tid] = pad_index(oy0 - 6 + tid, H, A.bc);
     else if (tid < UR + UCU) S.scol[b][tid - UR] = pad_index(ox0 - 6 + tid - UR, W, A.bc);
     __syncthreads();
@@ -492,15 +497,15 @@ __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF> &S, 
 // Issue the asynchronous copies of the output-pass operands (delta, d) of the tile whose geometry is in buffer b
 // (all threads; the caller commits).  The operand buffer is single: these are issued once the previous tile's
 // output pass is over, and are first needed at the end of the tile's own pipeline.
-template <int MODE, bool TF>
-__device__ __forceinline__ void stage_operands(const LaunchArgs &A, TcSmem<TF> &S, int b, int warp, int lane)
+template <int MODE, bool TF, int TOH>
+__device__ __forceinline__ void stage_operands(const LaunchArgs &A, TcSmem<TF, TOH> &S, int b, int warp, int lane)
 {
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
     const int H = D.H, W = D.W, ld = D.ld;
     if (lane < TO) {
         const int gx = ox0 + lane;
-        for (int r = warp; r < TcGeo<TF>::TOH; r += NWARP) {
+        for (int r = warp; r < TOH; r += NWARP) {
             const int gy = oy0 + r, j = r * TO + lane;
             if (gy >= H || gx >= W) continue;
             const size_t idx = (size_t)gy * ld + gx;
@@ -512,11 +517,11 @@ __device__ __forceinline__ void stage_operands(const LaunchArgs &A, TcSmem<TF> &
 
 // Persistent: CTA c processes tiles c, c + gridDim.x, ...; tensor memory, barriers and the filter operands
 // are set up once, and the input region of the next tile is copied in while the current one is computed.
-template <int MODE, bool TF>
+template <int MODE, bool TF, int TOH>
 __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem<TF> &S = *reinterpret_cast<TcSmem<TF> *>(smem_raw);
+    TcSmem<TF, TOH> &S = *reinterpret_cast<TcSmem<TF, TOH> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.tile_prefix[A.nimg];
     if ((int)blockIdx.x >= ntiles) return;
@@ -552,8 +557,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
         bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
     }
-    stage_input<TF>(A, S, blockIdx.x, 0, tid, warp, lane);
-    stage_operands<MODE, TF>(A, S, 0, warp, lane);
+    stage_input<TF, TOH>(A, S, blockIdx.x, 0, tid, warp, lane);
+    stage_operands<MODE, TF, TOH>(A, S, 0, warp, lane);
     cp_async_commit();
     fence_before();
     __syncthreads();
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (k > 0) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();
-        if (tile + (int)gridDim.x < ntiles) stage_input<TF>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+        if (tile + (int)gridDim.x < ntiles) stage_input<TF, TOH>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
         cp_async_commit();
 
         // ---- operand offset (BF16 range), then E ----
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int sidx = lane + 32 * h;
-                v += Ub[(2 + (kUR<TF> - 4) / 7 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
+                v += Ub[(2 + (kUR<TOH> - 4) / 7 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
             }
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) S.red[0] = v * (1.0f / 64.0f);
@@ -595,7 +600,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         const float mean = S.red[0];
         // one thread per 4 consecutive entries of an E row: the 11 inputs they span are loaded (three 16-byte
         // loads), shifted and rounded once
-        for (int item = tid; item < kUR<TF> * (RS / 4); item += NTHR) {
+        for (int item = tid; item < kUR<TOH> * (RS / 4); item += NTHR) {
             const int i = item / (RS / 4), x0 = 4 * (item % (RS / 4));
             const float4 *src = reinterpret_cast<const float4 *>(&Ub[i * UC + x0]);
             const float4 a0 = src[0], a1 = src[1], a2 = src[2];
@@ -636,8 +641,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     constexpr uint32_t IDF = TF ? idesc_tf32(128, 48) : idesc_bf16(128, 48);
                     const uint32_t e0 = smem_u32(S.E[0]), e1 = smem_u32(S.E[TcOps<TF>::EB - 1]);
                     const uint64_t dE = sdesc(e0, TF ? e1 - e0 : RS * 16, 128), dW = sdesc(smem_u32(S.Wf), 768, 128);
-                    for (int t = 0; ok && t < kNMT<TF>; ++t) {
-                        const int g = kNMT<TF> * k + t;
+                    for (int t = 0; ok && t < kNMT<TOH>; ++t) {
+                        const int g = kNMT<TOH> * k + t;
                         if (g >= 2 && !mbar_wait_warp(&S.bar[B_RFREE + (g & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
                         fence_after();
                         const uint32_t d = tmem + 64 * (g & 1);
@@ -660,8 +665,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     // or 8 tf32 filters)
                     constexpr uint32_t IDA = TF ? idesc_tf32(128, 64) : idesc_bf16(128, 64);
                     const uint64_t dWa = sdesc(smem_u32(S.Wa), 1024, 128);
-                    for (int t = 0; ok && t < kNMT<TF>; ++t) {
-                        const int g = kNMT<TF> * k + t;
+                    for (int t = 0; ok && t < kNMT<TOH>; ++t) {
+                        const int g = kNMT<TOH> * k + t;
                         if (!mbar_wait_warp(&S.bar[B_PSI + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                         if (g >= 2 && !mbar_wait_warp(&S.bar[B_ZFREE + (g & 1)], ((g - 2) >> 1) & 1, abort_flag, status)) break;
                         fence_after();
@@ -683,12 +688,12 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             const int q = warp & 3;
             // interior tile: the whole response region lies in the image, so no response is masked and no
             // lane outside 3..28 is ever read (no padding fold)
-            const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + kRR<TF> - 3 <= H && ox0 + RS - 3 <= W;
+            const bool interior = oy0 >= 3 && ox0 >= 3 && oy0 + kRR<TOH> - 3 <= H && ox0 + RS - 3 <= W;
             const uint32_t lane_base = (uint32_t)(32 * q) << 16;
             if (warp < 4) {
                 const int gx = ox0 - 3 + lane;
-                for (int t = 0; t < kNMT<TF>; ++t) {
-                    const int g = kNMT<TF> * k + t;
+                for (int t = 0; t < kNMT<TOH>; ++t) {
+                    const int g = kNMT<TOH> * k + t;
                     if (!mbar_wait(&S.bar[B_FWD + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                     fence_after();
                     const uint32_t rc = tmem + lane_base + 64 * (g & 1);
@@ -731,8 +736,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     mbar_arrive(&S.bar[B_PSI + (g & 1)]);
                 }
             } else {
-                for (int t = 0; t < kNMT<TF>; ++t) {
-                    const int g = kNMT<TF> * k + t;
+                for (int t = 0; t < kNMT<TOH>; ++t) {
+                    const int g = kNMT<TOH> * k + t;
                     if (!mbar_wait(&S.bar[B_ADJ + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                     fence_after();
                     float z[56];
@@ -758,7 +763,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                         }
 #pragma unroll
                         for (int a = 0; a < 7; ++a)
-                            hs_put(S.Hs[(a * kRR<TF> + rr) * RS + lane],
+                            hs_put(S.Hs[(a * kRR<TOH> + rr) * RS + lane],
                                    ((z[8 * a + 3] + sh[a][0]) + (sh[a][1] + sh[a][2])) + ((sh[a][3] + sh[a][4]) + sh[a][5]));
                     } else {
 #pragma unroll
@@ -773,7 +778,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                                 const float v = __shfl_sync(0xffffffffu, za[bb], src & 31);
                                 h += (src >= 0 && src < 32) ? v : 0.0f;
                             }
-                            hs_put(S.Hs[(a * kRR<TF> + rr) * RS + lane], h);
+                            hs_put(S.Hs[(a * kRR<TOH> + rr) * RS + lane], h);
                         }
                     }
                 }
@@ -788,7 +793,6 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // ---------------- output pass: vertical col2im, padding fold, iPiano step ----------------
         // warp w handles output rows w, w + 9/10, w + 2*(9/10) (lane = column): the rows are unrolled so that their
         // independent update chains interleave
-        constexpr int TOH = TcGeo<TF>::TOH;
         const bool ring = A.bc == kSymmetric && (oy0 < 3 || ox0 < 3 || oy0 + TOH > H - 3 || ox0 + TO > W - 3);
         constexpr int NR = (TOH + NWARP - 1) / NWARP;
         if (lane < TO) {
@@ -832,7 +836,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
-        if (tile + (int)gridDim.x < ntiles) stage_operands<MODE, TF>(A, S, buf ^ 1, warp, lane);
+        if (tile + (int)gridDim.x < ntiles) stage_operands<MODE, TF, TOH>(A, S, buf ^ 1, warp, lane);
         cp_async_commit();
     }
 
@@ -858,47 +862,91 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 
 // Dynamic shared memory per CTA.  At most two CTAs share an SM (2 x 256 TMEM columns); the request is
 // raised so that a third CTA, which would wait in tcgen05.alloc, is never made resident.
-template <bool TF>
+template <bool TF, int TOH>
 constexpr size_t smem_request()
 {
-    return sizeof(TcSmem<TF>) > 80 * 1024 ? sizeof(TcSmem<TF>) : 80 * 1024;
+    return sizeof(TcSmem<TF, TOH>) > 80 * 1024 ? sizeof(TcSmem<TF, TOH>) : 80 * 1024;
+}
+
+template <int MODE, bool TF, int TOH>
+cudaError_t tc_launch_one(const LaunchArgs &a, int grid, int *d_status, cudaStream_t s)
+{
+    k_foe_tc<MODE, TF, TOH><<<grid, NTHR, smem_request<TF, TOH>(), s>>>(a, d_status);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool TF, int TOH>
+cudaError_t tc_attr()
+{
+    return cudaFuncSetAttribute(k_foe_tc<MODE, TF, TOH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_request<TF, TOH>());
 }
 
 }  // namespace
 
-int tc_tile_h(bool tf32) { return tf32 ? TcGeo<true>::TOH : TcGeo<false>::TOH; }
+int tc_tile_h(bool tf32, int H) { return !tf32 && H >= 4 * kTallH ? kTallH : kShortH; }
 int tc_tile_w() { return TO; }
-size_t tc_smem_bytes() { return smem_request<false>(); }
+size_t tc_smem_bytes() { return smem_request<false, kTallH>(); }
 
 cudaError_t tc_setup()
 {
     cudaError_t e;
-    const int b16 = (int)smem_request<false>(), t32 = (int)smem_request<true>();
-    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
-    if ((e = cudaFuncSetAttribute(k_foe_tc<kGrad, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16))) return e;
-    if ((e = cudaFuncSetAttribute(k_foe_tc<kStep, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32))) return e;
-    return cudaFuncSetAttribute(k_foe_tc<kGrad, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32);
+    if ((e = tc_attr<kStep, false, kTallH>())) return e;
+    if ((e = tc_attr<kGrad, false, kTallH>())) return e;
+    if ((e = tc_attr<kStep, false, kShortH>())) return e;
+    if ((e = tc_attr<kGrad, false, kShortH>())) return e;
+    if ((e = tc_attr<kStep, true, kShortH>())) return e;
+    return tc_attr<kGrad, true, kShortH>();
 }
+
+namespace {
+
+// One kernel launch over the images of `a` whose tiles are h rows tall (all of them if `all`).
+cudaError_t tc_launch_height(const LaunchArgs &a, int mode, bool tf32, int h, bool all, int slots, int *d_status,
+                             cudaStream_t s)
+{
+    const LaunchArgs *p = &a;
+    LaunchArgs b;
+    if (!all) {
+        b = a;
+        b.nimg = 0;
+        b.tile_prefix[0] = 0;
+        for (int i = 0; i < a.nimg; ++i) {
+            if (a.img[i].tile_h != h) continue;
+            b.img[b.nimg] = a.img[i];
+            b.tile_prefix[b.nimg + 1] = b.tile_prefix[b.nimg] + (a.tile_prefix[i + 1] - a.tile_prefix[i]);
+            b.nimg++;
+        }
+        p = &b;
+    }
+    const int tiles = p->tile_prefix[p->nimg];
+    if (tiles <= 0) return cudaSuccess;
+    const int grid = std::min(tiles, slots);
+    if (tf32) return mode == kStep ? tc_launch_one<kStep, true, kShortH>(*p, grid, d_status, s)
+                                   : tc_launch_one<kGrad, true, kShortH>(*p, grid, d_status, s);
+    if (h == kTallH) return mode == kStep ? tc_launch_one<kStep, false, kTallH>(*p, grid, d_status, s)
+                                          : tc_launch_one<kGrad, false, kTallH>(*p, grid, d_status, s);
+    return mode == kStep ? tc_launch_one<kStep, false, kShortH>(*p, grid, d_status, s)
+                         : tc_launch_one<kGrad, false, kShortH>(*p, grid, d_status, s);
+}
+
+}  // namespace
 
 cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s)
 {
-    const int tiles = a.tile_prefix[a.nimg];
-    if (tiles <= 0) return cudaSuccess;
+    if (a.nimg <= 0 || a.tile_prefix[a.nimg] <= 0) return cudaSuccess;
     if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
-    const int grid = std::min(tiles, 2 * sms);
-    if (tf32) {
-        if (mode == kStep) k_foe_tc<kStep, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
-        else k_foe_tc<kGrad, true><<<grid, NTHR, smem_request<true>(), s>>>(a, d_status);
-    } else {
-        if (mode == kStep) k_foe_tc<kStep, false><<<grid, NTHR, smem_request<false>(), s>>>(a, d_status);
-        else k_foe_tc<kGrad, false><<<grid, NTHR, smem_request<false>(), s>>>(a, d_status);
-    }
-    return cudaGetLastError();
+    const int slots = 2 * sms;  // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
+    int ntall = 0;
+    for (int i = 0; i < a.nimg; ++i) ntall += a.img[i].tile_h == kTallH;
+    if (ntall == 0 || ntall == a.nimg)
+        return tc_launch_height(a, mode, tf32, ntall ? kTallH : kShortH, true, slots, d_status, s);
+    if ((e = tc_launch_height(a, mode, tf32, kTallH, false, slots, d_status, s)) != cudaSuccess) return e;
+    return tc_launch_height(a, mode, tf32, kShortH, false, slots, d_status, s);
 }
 
 }  // namespace foe
