@@ -5,11 +5,16 @@ Workload (one "step"): the 512x512 set of the paper's noise levels -- peaks {1, 
 denoised as two batches through the C ABI (foe_denoise_batch).  Metric: MPix.iter/s, i.e.
 pixels x iterations per second (whole job, inputs already in HBM; L2 flushed between steps).
 
-Printed as one JSON line on rank 0.  Extra keys: the plain-FP32 path on the same workload, the
-single-image latency, the roofline of the fused step kernel, the FP64 oracle on the host cores,
-an end-to-end figure through the public API with host buffers, and the SM clocks seen meanwhile.
+Printed as one JSON line on rank 0.  Extra keys:
+  - the TF32 and plain-FP32 paths on the same workload, and the single-image latency;
+  - the roofline of the fused step kernel;
+  - the FP64 oracle on the host cores;
+  - an end-to-end figure through the public API with host buffers;
+  - 64 uneven images in one CUDA graph, the training step (unrolled and implicit-differentiation gradients),
+    the continuous-batching server, the binning variant and backtracking step control;
+  - the SM clocks seen meanwhile.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16|tf32|fp32]
 """
 from __future__ import annotations
 
