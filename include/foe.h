@@ -316,6 +316,18 @@ FOE_API foe_status foe_profile_read(foe_ctx *ctx, double *loop_ms, long *launche
 
 FOE_API const char *foe_status_string(foe_status s);
 
+/* Device-side status of the context: every wait of the tensor-core kernel is bounded, and one that expires records
+ * FOE_ETIMEOUT in a status word that makes every later launch of the context return at once (a sticky failure).
+ * A call with a report reads and clears it; foe_device_status does the same for calls without one: it
+ * synchronises the stream, returns FOE_OK or the recorded status, and clears it so that the context is usable
+ * again. */
+FOE_API foe_status foe_device_status(foe_ctx *ctx, void *stream);
+
+/* Failure-detection test aid: the next tensor-core launch of the context withholds one mbarrier arrival in one CTA,
+ * so that its bounded waits expire (after about 2 s) and the launch records FOE_ETIMEOUT.  Nothing faults, traps or
+ * hangs: the CTA drains its MMAs, frees its tensor memory and returns; the other CTAs finish normally. */
+FOE_API foe_status foe_debug_withhold_arrival(foe_ctx *ctx);
+
 /* Last error text of the context (never NULL). */
 FOE_API const char *foe_last_error(const foe_ctx *ctx);
 

@@ -352,6 +352,27 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     return FOE_OK;
 }
 
+foe_status foe_device_status(foe_ctx *c, void *stream)
+{
+    if (!c) return FOE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev_status = 0;
+    FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FOE_CUDA(c, cudaStreamSynchronize(s));
+    if (!dev_status) return FOE_OK;
+    FOE_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    FOE_CUDA(c, cudaStreamSynchronize(s));
+    set_err(c, "a device-side wait expired");
+    return (foe_status)dev_status;
+}
+
+foe_status foe_debug_withhold_arrival(foe_ctx *c)
+{
+    if (!c) return FOE_EINVAL;
+    c->withhold_arrival = 1;
+    return FOE_OK;
+}
+
 foe_status foe_denoise_binned(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
                               const foe_solve_opts *o, void *stream, foe_report *rep)
 {

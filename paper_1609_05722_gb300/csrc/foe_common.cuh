@@ -48,6 +48,8 @@ struct LaunchArgs {
     int bc;
     int nchunks;               // ceil(nf / 8)
     int prior_only;            // kGrad / kEnergy: the FoE prior term alone (no data term), 0 otherwise
+    int withhold_arrival;      // failure-detection test: CTA 0 of the tensor-core step withholds one mbarrier
+                               // arrival, so that a bounded wait expires (0 otherwise)
     const float *wts;          // device [48][49], correlation form w_i(a, b) = k_i(-a, -b)
     const float *alpha;        // device [48]
     double *partials;          // kEnergy: one FP64 partial per tile

@@ -34,6 +34,7 @@ struct foe_ctx {
     int partials_cap = 0;
     double *d_energy = nullptr;
     int *d_status = nullptr;
+    int withhold_arrival = 0;               // foe_debug_withhold_arrival: applies to the next tensor-core launch
     LaunchArgs args;
     // step-loop timing (foe_profile)
     bool prof = false;
@@ -256,6 +257,7 @@ inline void args_begin(foe_ctx *c, int bc)
     A.bc = bc;
     A.nchunks = (c->nf + 7) / 8;
     A.prior_only = 0;
+    A.withhold_arrival = 0;
     A.wts = c->d_wts;
     A.alpha = c->d_alpha;
     A.partials = c->d_partials;
@@ -280,8 +282,15 @@ inline void args_add(foe_ctx *c, int prec, const ImgDesc &d)
 
 inline foe_status launch(foe_ctx *c, int prec, int mode, cudaStream_t s)
 {
-    cudaError_t e = prec == FOE_PREC_FP32 ? foe::f32_launch(c->args, mode, s)
-                                          : foe::tc_launch(c->args, mode, prec == FOE_PREC_TF32, c->d_status, s);
+    cudaError_t e;
+    if (prec == FOE_PREC_FP32) {
+        e = foe::f32_launch(c->args, mode, s);
+    } else {
+        c->args.withhold_arrival = c->withhold_arrival;
+        c->withhold_arrival = 0;
+        e = foe::tc_launch(c->args, mode, prec == FOE_PREC_TF32, c->d_status, s);
+        c->args.withhold_arrival = 0;
+    }
     if (e != cudaSuccess) {
         set_err(c, "kernel launch failed: %s", cudaGetErrorString(e));
         return e == cudaErrorNotSupported ? FOE_EUNSUPPORTED : FOE_ECUDA;

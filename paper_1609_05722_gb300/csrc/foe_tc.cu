@@ -674,7 +674,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
                         for (int kk = 0; kk < (TF ? 6 : 3); ++kk)
                             mma_ta_elect<TF>(d, a + 8 * kk, dWa + (uint64_t)(kk * 128), IDA, kk > 0);
-                        commit_elect(&S.bar[B_ADJ + (g & 1)]);
+                        // (a failure-detection test makes CTA 0 withhold this arrival once: the col2im warps' bounded
+                        // wait then expires and the launch reports FOE_ETIMEOUT)
+                        if (!(A.withhold_arrival && blockIdx.x == 0 && g == 0)) commit_elect(&S.bar[B_ADJ + (g & 1)]);
                         commit_elect(&S.bar[B_RFREE + (g & 1)]);
                     }
                 }

@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
             "foe_prior_lipschitz": (i, [C.POINTER(foe_prior), i, C.POINTER(d)]),
             "foe_step_log": (i, [vp, C.POINTER(f), C.POINTER(C.c_ubyte), i]),
             "foe_denoise": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
+            "foe_device_status": (i, [vp, vp]),
+            "foe_debug_withhold_arrival": (i, [vp]),
             "foe_denoise_binned": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
             "foe_denoise_batch": (i, [vp, C.POINTER(foe_image_desc), i, C.POINTER(foe_solve_opts), vp]),
             "foe_energy_grad": (i, [vp, vp, vp, i, i, i, i, f, i, i, C.POINTER(d), vp, vp]),
@@ -145,6 +147,16 @@ def foe_status_string(status: int) -> str:
 
 def foe_last_error(ctx) -> str:
     return lib().foe_last_error(ctx).decode()
+
+
+def foe_device_status(ctx, stream=None) -> int:
+    """Reads and clears the context's device-side status (FOE_OK or FOE_ETIMEOUT); synchronises the stream."""
+    return lib().foe_device_status(ctx, _stream(stream))
+
+
+def foe_debug_withhold_arrival(ctx) -> None:
+    """Failure-detection test aid: the next tensor-core launch lets one bounded device wait expire."""
+    _check(lib().foe_debug_withhold_arrival(ctx), ctx, "foe_debug_withhold_arrival")
 
 
 @dataclass
