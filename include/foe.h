@@ -103,6 +103,7 @@ typedef struct {
     foe_status status;
     int backtracks;       /* BACKTRACK: rejected trials (0 for FIXED) */
     double lipschitz_final; /* BACKTRACK: L after the last step; FIXED: the L that tau_used corresponds to */
+    int nonfinite;        /* non-finite output pixels (NaN / Inf sentinel); the call then returns FOE_ENONFINITE */
 } foe_report;
 
 /* One image of a batch (foe_denoise_batch). */
@@ -147,7 +148,8 @@ FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted
  *   y    device, noisy counts (non-negative integers stored as FP32), H x W, pitch ld
  *   x    device, output in the intensity domain, H x W, pitch ld (may alias y)
  *   peak the noise level (max of the clean image, Sec. 2.1); only FOE_MODEL_AUTO reads it
- *   rep  host, nullable; if given, the stream is synchronised and the report filled
+ *   rep  host, nullable; if given, the stream is synchronised and the report filled, and the call also returns
+ *        FOE_ETIMEOUT for an expired device-side wait and FOE_ENONFINITE if any output pixel is not finite
  * opts.step = FOE_STEP_BACKTRACK (FP32 only; step a9): the step size of iPiano (Sec. 2.3, given there only as a
  * symbol) is found per iteration by Lipschitz backtracking on the smooth part F = E_FoE: a trial with estimate
  * L uses tau = 2 (1 - gamma) / (L + 2e-3) and is accepted when

@@ -56,7 +56,7 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
     for (int j = 0; j < n; ++j) {
         const foe_image_desc &d = descs[order[j]];
         const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0;
-        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, slots[j].ul), d.H, d.W, d.ld, d.ld, models[j], d.x, s));
+        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, slots[j].ul), d.H, d.W, d.ld, d.ld, models[j], d.x, nullptr, s));
     }
     return FOE_OK;
 }
@@ -134,7 +134,7 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         (e = cudaMemcpy(c->d_tcops, ops.data(), ops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice)) ||
         (e = cudaMalloc(&c->d_tcops32, ops32.size() * sizeof(uint32_t))) ||
         (e = cudaMemcpy(c->d_tcops32, ops32.data(), ops32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) ||
-        (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) ||
+        (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) || (e = cudaMalloc(&c->d_nonfinite, sizeof(int))) ||
         (e = cudaMemcpy(c->d_wts, w, sizeof(w), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(c->d_status, 0, sizeof(int))) || (e = foe::f32_setup()) || (e = foe::tc_setup()) || (e = foe::bwd_setup()))
@@ -155,6 +155,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_tcops32);
     cudaFree(c->d_energy);
     cudaFree(c->d_status);
+    cudaFree(c->d_nonfinite);
     cudaFree(c->d_partials);
     cudaFree(c->ws);
     cudaFree(c->d_bin);
@@ -275,17 +276,24 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         std::swap(cur, nxt);
         L /= 1.5;
     }
-    FOE_CUDA(c, foe::launch_output(cur, sl.ul, H, W, ld, ld, model, x, s));
+    if (rep) FOE_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), s));
+    FOE_CUDA(c, foe::launch_output(cur, sl.ul, H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s));
     if (rep) {
-        int dev_status = 0;
+        int dev_status = 0, nonfinite = 0;
         FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FOE_CUDA(c, cudaMemcpyAsync(&nonfinite, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaStreamSynchronize(s));
+        rep->nonfinite = nonfinite;
         rep->iters_done = o->iters;
         rep->model_used = model;
         rep->tau_used = tau;
         rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
         rep->backtracks = backtracks;
         rep->lipschitz_final = L;
+        if (nonfinite) {
+            set_err(c, "%d non-finite output pixels", nonfinite);
+            return FOE_ENONFINITE;
+        }
     }
     return FOE_OK;
 }
@@ -332,11 +340,14 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     }
     if ((st = prof_end(c, s, ev, o->iters, (double)H * W * o->iters)) != FOE_OK) return st;
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
-    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, s));
+    if (rep) FOE_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), s));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s));
     if (rep) {
-        int dev_status = 0;
+        int dev_status = 0, nonfinite = 0;
         FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FOE_CUDA(c, cudaMemcpyAsync(&nonfinite, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaStreamSynchronize(s));
+        rep->nonfinite = nonfinite;
         rep->iters_done = o->iters;
         rep->model_used = model;
         rep->tau_used = tau;
@@ -347,6 +358,10 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
             FOE_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
             set_err(c, "a device-side wait expired during the solve");
             return (foe_status)dev_status;
+        }
+        if (nonfinite) {
+            set_err(c, "%d non-finite output pixels", nonfinite);
+            return FOE_ENONFINITE;
         }
     }
     return FOE_OK;
@@ -683,7 +698,7 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
         if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
     }
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
-    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, s));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, nullptr, s));
     return FOE_OK;
 }
 

@@ -262,13 +262,17 @@ __device__ __forceinline__ double inv_anscombe(double z)
 }
 
 // Output map: x = I_C(max(u, sqrt(3/2))) (Eq. invAns) for the Anscombe models, x = u for the direct one.
-__global__ void k_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x)
+// Output map; counts the non-finite outputs into *nonfinite when it is given (a NaN / Inf sentinel).
+__global__ void k_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x,
+                         int *nonfinite)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (c >= W || r >= H) return;
     const size_t i = (size_t)r * ld + c;
     const double u = (double)uh[i] + (ul ? (double)ul[i] : 0.0);
-    x[(size_t)r * xld + c] = model == kDirect ? (float)u : (float)inv_anscombe(u);
+    const float v = model == kDirect ? (float)u : (float)inv_anscombe(u);
+    x[(size_t)r * xld + c] = v;
+    if (nonfinite && !isfinite(v)) atomicAdd(nonfinite, 1);
 }
 
 __global__ void k_anscombe(const float *y, float *v, long n)
@@ -332,11 +336,11 @@ cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model
     return cudaGetLastError();
 }
 
-cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x,
+cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x, int *nonfinite,
                           cudaStream_t s)
 {
     dim3 g((W + 127) / 128, H);
-    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x);
+    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x, nonfinite);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ struct foe_ctx {
     int partials_cap = 0;
     double *d_energy = nullptr;
     int *d_status = nullptr;
+    int *d_nonfinite = nullptr;             // non-finite outputs of the last reporting solve
     int withhold_arrival = 0;               // foe_debug_withhold_arrival: applies to the next tensor-core launch
     LaunchArgs args;
     // step-loop timing (foe_profile)

@@ -290,7 +290,7 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
         }
         const Slot sl = request_slot(sv, r);
         const float *uf = (r->iters & 1) ? sl.uh1 : sl.uh0;
-        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o.prec, sl.ul), r->H, r->W, r->ld, r->ld, r->model, sl.delta, sv->stream));
+        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o.prec, sl.ul), r->H, r->W, r->ld, r->ld, r->model, sl.delta, nullptr, sv->stream));
         FOE_CUDA(c, cudaMemcpy2DAsync(r->x_host, r->x_pitch * sizeof(float), sl.delta, r->ld * sizeof(float),
                                       r->W * sizeof(float), r->H, cudaMemcpyDeviceToHost, sv->stream));
         finished.push_back(r);

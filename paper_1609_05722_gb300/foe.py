@@ -38,7 +38,7 @@ class foe_solve_opts(C.Structure):
 
 class foe_report(C.Structure):
     _fields_ = [("iters_done", C.c_int), ("model_used", C.c_int), ("tau_used", C.c_float), ("status", C.c_int),
-                ("backtracks", C.c_int), ("lipschitz_final", C.c_double)]
+                ("backtracks", C.c_int), ("lipschitz_final", C.c_double), ("nonfinite", C.c_int)]
 
 
 class foe_image_desc(C.Structure):
@@ -229,7 +229,8 @@ def foe_denoise(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: SolveOpts
                              C.byref(rep) if report else None), ctx, "foe_denoise")
     if report:
         return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
-                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final}
+                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final,
+                "nonfinite": rep.nonfinite}
     return None
 
 
@@ -242,7 +243,8 @@ def foe_denoise_binned(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: So
                                     C.byref(rep) if report else None), ctx, "foe_denoise_binned")
     if report:
         return {"iters_done": rep.iters_done, "model_used": rep.model_used, "tau_used": rep.tau_used,
-                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final}
+                "status": rep.status, "backtracks": rep.backtracks, "lipschitz_final": rep.lipschitz_final,
+                "nonfinite": rep.nonfinite}
     return None
 
 

@@ -92,3 +92,21 @@ def test_resume_from_a_host_checkpoint_is_bitwise_identical(ctx, prec, tmp_path)
     torch.cuda.synchronize()
     for a, b in zip(straight, resumed):  # image columns (the pitch padding of fresh outputs is never written)
         assert torch.equal(a[:, :W], b[:, :W])
+
+
+@pytest.mark.parametrize("prec", [F.FOE_PREC_FP32, F.FOE_PREC_BF16])
+def test_non_finite_outputs_are_reported(ctx, prec):
+    # a NaN in the data spreads through the responses of its neighbourhood; with a report the call counts the
+    # non-finite outputs and returns FOE_ENONFINITE (without one it returns normally)
+    H = W = 48
+    y = _image(H, W, 51)
+    y[20, 20] = float("nan")
+    x = torch.zeros_like(y)
+    opts = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=prec, iters=3)
+    F.foe_denoise(ctx, y, x, H, W, W, 4.0, opts)
+    with pytest.raises(F.FoeError) as e:
+        F.foe_denoise(ctx, y, x, H, W, W, 4.0, opts, report=True)
+    assert e.value.status == F.FOE_ENONFINITE
+    assert int((~torch.isfinite(x)).sum()) > 1
+    rep = F.foe_denoise(ctx, _image(H, W, 52), x, H, W, W, 4.0, opts, report=True)
+    assert rep["nonfinite"] == 0 and F.foe_device_status(ctx) == F.FOE_OK
