@@ -301,6 +301,7 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
 foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *o, void *stream, foe_report *rep)
 {
+    NvtxRange nvtx_range("foe_denoise");
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts(c, o)) != FOE_OK) return st;
@@ -391,6 +392,7 @@ foe_status foe_debug_withhold_arrival(foe_ctx *c)
 foe_status foe_denoise_binned(foe_ctx *c, const float *y, float *x, int H, int W, int ld, float peak,
                               const foe_solve_opts *o, void *stream, foe_report *rep)
 {
+    NvtxRange nvtx_range("foe_denoise_binned");
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts(c, o)) != FOE_OK) return st;
@@ -417,6 +419,7 @@ foe_status foe_denoise_binned(foe_ctx *c, const float *y, float *x, int H, int W
 
 foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, const foe_solve_opts *o, void *stream)
 {
+    NvtxRange nvtx_range("foe_denoise_batch");
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(c, o, "foe_denoise_batch")) != FOE_OK) return st;

@@ -11,6 +11,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/foe.h"
 #include "foe_kernels.h"
 
@@ -50,6 +52,14 @@ struct foe_ctx {
 };
 
 namespace foe_internal {
+
+// NVTX range over a C-ABI call: a named span on a profiler's timeline (no cost when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline void set_err(foe_ctx *c, const char *fmt, ...)
 {

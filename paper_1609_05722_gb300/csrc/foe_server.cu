@@ -229,6 +229,7 @@ foe_status foe_server_submit(foe_server *sv, const float *y_host, int y_pitch, f
 
 foe_status foe_server_tick(foe_server *sv, int *n_completed)
 {
+    NvtxRange nvtx_range("foe_server_tick");
     if (!sv) return FOE_EINVAL;
     foe_ctx *c = sv->ctx;
     const foe_solve_opts &o = sv->cfg.opts;

@@ -21,6 +21,7 @@ extern "C" foe_status foe_train_step(foe_ctx *c, const float *clean, const float
                                      const foe_solve_opts *o, int ckpt_every, double *loss_host, float *dfilters,
                                      float *dlogalpha, void *stream)
 {
+    NvtxRange nvtx_range("foe_train_step");
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(c, o, "foe_train_step")) != FOE_OK) return st;
@@ -169,6 +170,7 @@ extern "C" foe_status foe_train_grad_implicit(foe_ctx *c, const float *clean, co
                                               double *loss_host, float *dfilters, float *dlogalpha,
                                               foe_implicit_report *rep, void *stream)
 {
+    NvtxRange nvtx_range("foe_train_grad_implicit");
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(c, o, "foe_train_grad_implicit")) != FOE_OK) return st;
