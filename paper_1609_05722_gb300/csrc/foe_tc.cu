@@ -18,19 +18,19 @@
 //
 // Roles (320 threads): warps 0-7 move data between tensor memory and registers (warps w and w+4 access
 // TMEM lanes 32(w%4)..32(w%4)+31, i.e. response row 4t+w%4 of M-tile t): warps 0-3 run the expert step,
-// warps 4-7 the col2im.  One thread of warp 8 issues the forward MMAs and one thread of warp 9 the
-// adjoint MMAs, so neither kind of MMA waits behind the other's dependencies.
-// Tensor memory holds two response stages (columns 0 and 64) and two adjoint stages Z(g & 1) (columns
-// 128 and 192).  The epilogue writes Psi(t) (packed bf16 pairs, or tf32) over the first columns of R(t)'s
-// stage, and the adjoint MMA reads its A operand from there, so Psi never passes through shared memory;
-// the stage is free again once that MMA is complete, Z(t) once the col2im has loaded it.  Expert and
+// warps 4-7 the col2im.  Warp 8 issues the forward MMAs and warp 9 the adjoint MMAs (one elected lane each), so
+// neither kind of MMA waits behind the other's dependencies.
+// Tensor memory holds two response stages (columns 0 and 64) and two adjoint stages (columns 128 and 192); M-tile g
+// (counted over all tiles of the CTA) uses stage g & 1.  The epilogue writes Psi(g) (packed bf16 pairs, or tf32)
+// over the first columns of R(g)'s stage, and the adjoint MMA reads its A operand from there, so Psi never passes
+// through shared memory; the stage is free again once that MMA is complete, Z(g) once the col2im has loaded it.  Expert and
 // col2im warps run decoupled, so the MMAs of later M-tiles overlap the epilogue of earlier ones.
 // Every mbarrier wait is bounded: on expiry the CTA records FOE_ETIMEOUT in *status, drains its MMAs,
 // frees its tensor memory and finishes without further waits.
 //
 // BF16 range: filters are zero-mean, so K(u - c) = K u for any constant c (the padded image of a
 // constant is constant under symmetric padding; under zero padding the padded zeros are shifted by -c
-// too).  The tile mean is subtracted before rounding u to BF16.
+// too).  The mean of 64 samples of the tile's input region is subtracted before rounding u to BF16 / TF32.
 #include <algorithm>
 #include <cstdint>
 
