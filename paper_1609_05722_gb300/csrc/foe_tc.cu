@@ -114,6 +114,8 @@ struct TcSmem {
     float O[2][TO * TOH];                          // output-pass operands delta, d (staged after the previous tile)
     int srow[2][kUR<TOH>], scol[2][RS + 7];        // source row / column of each region row / column (-1: zero)
     int geo[2][4];                                 // image, oy0, ox0, write limit xe of the tile in buffer b
+    int tprefix[kMaxBatch + 1];                    // the launch's tile prefix, and per image: tiles per row, H, W
+    int timg[kMaxBatch][3];
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -130,6 +132,7 @@ using SmemTf32 = TcSmem<true, kShortH>;
 static_assert(offsetof(SmemBf16Tall, Wa) == offsetof(SmemBf16Tall, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
 static_assert(offsetof(SmemBf16, Wa) == offsetof(SmemBf16, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
 static_assert(offsetof(SmemTf32, Wa) == offsetof(SmemTf32, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
+static_assert(offsetof(SmemBf16Tall, U) % 8 == 0 && offsetof(SmemBf16, U) % 8 == 0 && offsetof(SmemTf32, U) % 8 == 0 && UC % 2 == 0 && UC >= 40, "");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -309,6 +312,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -447,21 +455,29 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF, TOH> &S, int qy, int
 // only if the tile reaches that border: the last tile of a row is therefore placed flush right (origin W - 26)
 // and the tile before it writes only the columns left of that origin.  Rows need no such rule: the vertical part
 // of the col2im reads response rows, and the rows that a reflection asks for that lie in the image are always
-// within 3 rows of the output row.
-template <int TOH>
-__device__ __forceinline__ void tile_geometry(const LaunchArgs &A, int tile, int &im, int &oy0, int &ox0, int &xe)
+// within 3 rows of the output row.  The lookup reads the launch's tile table from its copy in shared memory,
+// made at the start of the kernel: parameter-space loads here sat on the staging thread's dependent chain.
+template <bool TF, int TOH>
+__device__ __forceinline__ void tile_geometry(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int tile, int &im,
+                                              int &oy0, int &ox0, int &xe)
 {
-    im = tile_image(A, tile);
-    const ImgDesc &D = A.img[im];
-    const int lt = tile - A.tile_prefix[im];
-    const int tx = lt % D.tiles_x;
-    oy0 = (lt / D.tiles_x) * TOH;
+    int lo = 0, hi = A.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.tprefix[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    im = lo;
+    const int tiles_x = S.timg[im][0], W = S.timg[im][2];
+    const int lt = tile - S.tprefix[im];
+    const int tx = lt % tiles_x;
+    oy0 = (lt / tiles_x) * TOH;
     ox0 = tx * TO;
-    xe = min(ox0 + TO, D.W);
-    if (D.W > TO) {
-        const int last = D.W - TO;
+    xe = min(ox0 + TO, W);
+    if (W > TO) {
+        const int last = W - TO;
         ox0 = min(ox0, last);
-        xe = tx + 1 < D.tiles_x ? min(xe, last) : D.W;
+        xe = tx + 1 < tiles_x ? min(xe, last) : W;
     }
 }
 
@@ -472,7 +488,7 @@ template <bool TF, int TOH>
 __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH> &S, int tile, int b, int tid, int warp,
                                             int lane)
 {
-    if (tid == 0) tile_geometry<TOH>(A, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
+    if (tid == 0) tile_geometry(A, S, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
     __syncthreads();
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
@@ -483,13 +499,30 @@ __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH>
     __syncthreads();
     const float *uin = D.u_hi[A.parity];
     float *U = S.U[b];
-    for (int r = warp; r < UR; r += NWARP) {
-        const int sy = S.srow[b][r];
-        const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
-        for (int c = lane; c < UCU; c += 32) {
-            const int sx = S.scol[b][c];
-            if (sy < 0 || sx < 0) U[r * UC + c] = 0.0f;
-            else cp_async4(&U[r * UC + c], src + sx);
+    if (ox0 >= 6 && ((ox0 - 6) & 1) == 0 && ox0 + 34 <= W) {
+        // the region's columns ox0 - 6 .. ox0 + 33 lie in the image (no reflection) and start 8-byte aligned (the
+        // API takes 16-byte aligned images with a pitch of a multiple of 4 floats): 20 lanes copy 8 bytes of each
+        // row, one warp instruction per row instead of two (column 39 is copied but not used)
+        if (lane < 20) {
+            for (int r = warp; r < UR; r += NWARP) {
+                const int sy = S.srow[b][r];
+                float *dst = &U[r * UC + 2 * lane];
+                if (sy < 0) *reinterpret_cast<float2 *>(dst) = make_float2(0.0f, 0.0f);
+                else cp_async8(dst, uin + (size_t)sy * ld + ox0 - 6 + 2 * lane);
+            }
+        }
+    } else {
+        const int sx0 = S.scol[b][lane], sx1 = lane + 32 < UCU ? S.scol[b][lane + 32] : -1;
+        for (int r = warp; r < UR; r += NWARP) {
+            const int sy = S.srow[b][r];
+            const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
+            float *dst = &U[r * UC];
+            if (sy < 0 || sx0 < 0) dst[lane] = 0.0f;
+            else cp_async4(&dst[lane], src + sx0);
+            if (lane + 32 < UCU) {
+                if (sy < 0 || sx1 < 0) dst[lane + 32] = 0.0f;
+                else cp_async4(&dst[lane + 32], src + sx1);
+            }
         }
     }
 }
@@ -545,6 +578,13 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         }
         mbar_init(&S.bar[B_W], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the tile table for tile_geometry (read after the __syncthreads below)
+    if (tid <= A.nimg) S.tprefix[tid] = A.tile_prefix[tid];
+    if (tid < A.nimg) {
+        S.timg[tid][0] = A.img[tid].tiles_x;
+        S.timg[tid][1] = A.img[tid].H;
+        S.timg[tid][2] = A.img[tid].W;
     }
     if (warp == FWD_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
