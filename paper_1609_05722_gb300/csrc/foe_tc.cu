@@ -558,12 +558,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.tile_prefix[A.nimg];
     if ((int)blockIdx.x >= ntiles) return;
-
-    // an earlier launch that gave up leaves *status set: then do nothing (CTA-uniform decision)
-    if (tid == 0) S.abort_flag = *(volatile int *)status;
-    __syncthreads();
-    if (S.abort_flag) return;
-    __syncthreads();
+    // the next launch in the stream may be scheduled now; its CTAs take an SM as ours leave it and set up their
+    // barriers and tensor memory while the rest of this grid finishes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // ---- barriers, tensor memory, filter operands (one bulk copy) ----
     constexpr uint32_t WBYTES = sizeof(uint4) * (TcOps<TF>::WF + TcOps<TF>::WA);
@@ -592,7 +589,20 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // nothing above read memory that an earlier launch writes: from here on its results (the iterate, the filter
+    // operands, *status) are needed, so wait until that grid has completed and its writes are visible (returns at
+    // once when this launch has no programmatic dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // an earlier launch that gave up leaves *status set: then do nothing (CTA-uniform decision)
+    if (tid == 0) S.abort_flag = *(volatile int *)status;
     __syncthreads();
+    if (S.abort_flag) {
+        if (warp == FWD_WARP) {
+            const uint32_t tm = S.tmem_base;
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TMEM_COLS) : "memory");
+        }
+        return;
+    }
     if (tid == 0) {
         mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
         bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
@@ -913,8 +923,19 @@ constexpr size_t smem_request()
 template <int MODE, bool TF, int TOH>
 cudaError_t tc_launch_one(const LaunchArgs &a, int grid, int *d_status, cudaStream_t s)
 {
-    k_foe_tc<MODE, TF, TOH><<<grid, NTHR, smem_request<TF, TOH>(), s>>>(a, d_status);
-    return cudaGetLastError();
+    // programmatic dependent launch: the kernel waits (griddepcontrol.wait) for the preceding grid before it
+    // reads anything that grid may write
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NTHR);
+    cfg.dynamicSmemBytes = smem_request<TF, TOH>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_foe_tc<MODE, TF, TOH>, a, d_status);
 }
 
 template <int MODE, bool TF, int TOH>
