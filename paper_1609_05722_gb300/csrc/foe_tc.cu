@@ -102,7 +102,13 @@ constexpr int B_ADJ = 6;     // [2] adjoint MMAs of M-tile g complete (g & 1)   
 constexpr int B_ZFREE = 8;   // [2] Z(g) loaded by every col2im thread (g & 1)           count 128
 constexpr int B_W = 10;      // filter operand images arrived (bulk copy)                count 1 + tx
 constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread complete    count 1 (commit)
-constexpr int NBAR = 13;
+constexpr int B_UREADY = 13; // [2] input region of buffer b landed (every thread's copies) count NTHR (cp.async)
+constexpr int NBAR = 15;
+
+// E rows of a tile built by the expert warps at the end of the previous tile (while the last M-tile's adjoint
+// and col2im finish)
+template <int TOH>
+constexpr int kPreE = TOH >= 40 ? 40 : 24;
 
 template <bool TF, int TOH>
 struct TcSmem {
@@ -119,7 +125,7 @@ struct TcSmem {
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
-    float red[NWARP];
+    float meanb[2];                                // BF16 / TF32 range offset of the tile in buffer b
 };
 // Two CTAs share an SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
 static_assert(sizeof(TcSmem<false, kTallH>) + 1024 <= 228 * 1024 / 2, "BF16 tall tiles: two CTAs per SM");
@@ -317,6 +323,20 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// Zero fill through the copy engine (no bytes read): every store to the input region is then a cp.async, whose
+// completion the region's mbarrier tracks
+__device__ __forceinline__ void cp_async_zero(void *dst, const void *any, int bytes)
+{
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 0;" ::"r"(smem_u32(dst)), "l"(any) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 0;" ::"r"(smem_u32(dst)), "l"(any) : "memory");
+}
+
+// arrive on an mbarrier once all of this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -507,7 +527,7 @@ __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH>
             for (int r = warp; r < UR; r += NWARP) {
                 const int sy = S.srow[b][r];
                 float *dst = &U[r * UC + 2 * lane];
-                if (sy < 0) *reinterpret_cast<float2 *>(dst) = make_float2(0.0f, 0.0f);
+                if (sy < 0) cp_async_zero(dst, uin, 8);
                 else cp_async8(dst, uin + (size_t)sy * ld + ox0 - 6 + 2 * lane);
             }
         }
@@ -517,14 +537,65 @@ __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH>
             const int sy = S.srow[b][r];
             const float *src = uin + (size_t)(sy < 0 ? 0 : sy) * ld;
             float *dst = &U[r * UC];
-            if (sy < 0 || sx0 < 0) dst[lane] = 0.0f;
+            if (sy < 0 || sx0 < 0) cp_async_zero(&dst[lane], uin, 4);
             else cp_async4(&dst[lane], src + sx0);
             if (lane + 32 < UCU) {
-                if (sy < 0 || sx1 < 0) dst[lane + 32] = 0.0f;
+                if (sy < 0 || sx1 < 0) cp_async_zero(&dst[lane + 32], uin, 4);
                 else cp_async4(&dst[lane + 32], src + sx1);
             }
         }
     }
+    cp_async_mbar_arrive(&S.bar[B_UREADY + b]);
+}
+
+// E rows [r0, r1) of the tile whose input region is Ub, with range offset `mean`: one item = 4 consecutive entries
+// of an E row, whose 11 inputs are loaded (three 16-byte loads), shifted and rounded once.  Items idx, idx +
+// stride, ... of the range.
+template <bool TF, int TOH>
+__device__ __forceinline__ void build_e(TcSmem<TF, TOH> &S, const float *Ub, float mean, int r0, int r1, int idx,
+                                        int stride)
+{
+    for (int item = r0 * (RS / 4) + idx; item < r1 * (RS / 4); item += stride) {
+        const int i = item / (RS / 4), x0 = 4 * (item % (RS / 4));
+        const float4 *src = reinterpret_cast<const float4 *>(&Ub[i * UC + x0]);
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+        const float v[11] = {a0.x - mean, a0.y - mean, a0.z - mean, a0.w - mean, a1.x - mean, a1.y - mean,
+                             a1.z - mean, a1.w - mean, a2.x - mean, a2.y - mean, a2.z - mean};
+        uint4 *dst = &S.E[0][i * RS + x0];
+        if (TF) {
+            uint32_t c[11];
+#pragma unroll
+            for (int j2 = 0; j2 < 11; ++j2) c[j2] = to_tf32(v[j2]);
+            uint4 *dst1 = &S.E[TcOps<TF>::EB - 1][i * RS + x0];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                dst[e] = make_uint4(c[e], c[e + 1], c[e + 2], c[e + 3]);
+                dst1[e] = make_uint4(c[e + 4], c[e + 5], c[e + 6], c[e + 7]);
+            }
+        } else {
+            uint32_t pr[10];
+#pragma unroll
+            for (int j2 = 0; j2 < 10; ++j2) pr[j2] = pack_bf16x2(v[j2], v[j2 + 1]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pr[e], pr[e + 2], pr[e + 4], pr[e + 6]);
+        }
+    }
+}
+
+// Range offset of the tile whose input region is Ub (warp-collective; every lane gets it).  Any constant c gives
+// K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the mean of 64 samples of the
+// region (an 8 x 8 grid) serves.
+template <int TOH>
+__device__ __forceinline__ float region_mean(const float *Ub, int lane)
+{
+    float v = 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int sidx = lane + 32 * h;
+        v += Ub[(2 + (kUR<TOH> - 4) / 7 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v * (1.0f / 64.0f);
 }
 
 // Issue the asynchronous copies of the output-pass operands (delta, d) of the tile whose geometry is in buffer b
@@ -574,6 +645,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             mbar_init(&S.bar[B_DRAIN + b], 1);
         }
         mbar_init(&S.bar[B_W], 1);
+        mbar_init(&S.bar[B_UREADY], NTHR);
+        mbar_init(&S.bar[B_UREADY + 1], NTHR);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the tile table for tile_geometry (read after the __syncthreads below)
@@ -632,49 +705,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (tile + (int)gridDim.x < ntiles) stage_input<TF, TOH>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
         cp_async_commit();
 
-        // ---- operand offset (BF16 range), then E ----
-        // Any constant c gives K(u - c) = K u (zero-mean filters); c only sets the BF16 / TF32 rounding, so the
-        // mean of 64 samples of the region (an 8 x 8 grid) serves.
+        // ---- E: all rows for the first tile; for later ones the rows the expert warps did not build at the end of
+        // the previous tile ----
         const float *Ub = S.U[buf];
-        if (warp == 0) {
-            float v = 0.0f;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int sidx = lane + 32 * h;
-                v += Ub[(2 + (kUR<TOH> - 4) / 7 * (sidx >> 3)) * UC + 2 + 5 * (sidx & 7)];
+        if (k == 0) {
+            if (warp == 0) {
+                const float m = region_mean<TOH>(Ub, lane);
+                if (lane == 0) S.meanb[0] = m;
             }
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) S.red[0] = v * (1.0f / 64.0f);
+            __syncthreads();
         }
-        __syncthreads();
-        const float mean = S.red[0];
-        // one thread per 4 consecutive entries of an E row: the 11 inputs they span are loaded (three 16-byte
-        // loads), shifted and rounded once
-        for (int item = tid; item < kUR<TOH> * (RS / 4); item += NTHR) {
-            const int i = item / (RS / 4), x0 = 4 * (item % (RS / 4));
-            const float4 *src = reinterpret_cast<const float4 *>(&Ub[i * UC + x0]);
-            const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-            const float v[11] = {a0.x - mean, a0.y - mean, a0.z - mean, a0.w - mean, a1.x - mean, a1.y - mean,
-                                 a1.z - mean, a1.w - mean, a2.x - mean, a2.y - mean, a2.z - mean};
-            uint4 *dst = &S.E[0][i * RS + x0];
-            if (TF) {
-                uint32_t c[11];
-#pragma unroll
-                for (int j2 = 0; j2 < 11; ++j2) c[j2] = to_tf32(v[j2]);
-                uint4 *dst1 = &S.E[TcOps<TF>::EB - 1][i * RS + x0];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    dst[e] = make_uint4(c[e], c[e + 1], c[e + 2], c[e + 3]);
-                    dst1[e] = make_uint4(c[e + 4], c[e + 5], c[e + 6], c[e + 7]);
-                }
-            } else {
-                uint32_t pr[10];
-#pragma unroll
-                for (int j2 = 0; j2 < 10; ++j2) pr[j2] = pack_bf16x2(v[j2], v[j2 + 1]);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) dst[e] = make_uint4(pr[e], pr[e + 2], pr[e + 4], pr[e + 6]);
-            }
-        }
+        build_e(S, Ub, S.meanb[buf], k == 0 ? 0 : kPreE<TOH>, kUR<TOH>, tid, NTHR);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -744,6 +785,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
             const uint32_t lane_base = (uint32_t)(32 * q) << 16;
             if (warp < 4) {
                 const int gx = ox0 - 3 + lane;
+                bool done = false;
                 for (int t = 0; t < kNMT<TOH>; ++t) {
                     const int g = kNMT<TOH> * k + t;
                     if (!mbar_wait(&S.bar[B_FWD + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
@@ -786,6 +828,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     tmem_wait_st();
                     fence_before();
                     mbar_arrive(&S.bar[B_PSI + (g & 1)]);
+                    if (t == kNMT<TOH> - 1) done = true;
+                }
+                // every forward MMA of this tile is complete (each expert thread saw the last one), so E is free:
+                // the first rows of the next tile's E are built while the last adjoint and col2im finish
+                if (done && tile + (int)gridDim.x < ntiles &&
+                    mbar_wait(&S.bar[B_UREADY + (buf ^ 1)], ((k + 1) >> 1) & 1, abort_flag, status)) {
+                    const float m = region_mean<TOH>(S.U[buf ^ 1], lane);
+                    if (tid == 0) S.meanb[buf ^ 1] = m;
+                    build_e(S, S.U[buf ^ 1], m, 0, kPreE<TOH>, tid, 128);
                 }
             } else {
                 for (int t = 0; t < kNMT<TOH>; ++t) {
