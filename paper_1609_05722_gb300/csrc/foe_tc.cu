@@ -105,11 +105,6 @@ constexpr int B_DRAIN = 11;  // [2] all MMAs of the forward / adjoint thread com
 constexpr int B_UREADY = 13; // [2] input region of buffer b landed (every thread's copies) count NTHR (cp.async)
 constexpr int NBAR = 15;
 
-// E rows of a tile built by the expert warps at the end of the previous tile (while the last M-tile's adjoint
-// and col2im finish)
-template <int TOH>
-constexpr int kPreE = TOH >= 40 ? 40 : 24;
-
 template <bool TF, int TOH>
 struct TcSmem {
     uint4 E[TcOps<TF>::EB][kUR<TOH> * RS];  // forward A operand: entry (row, x) holds u(row, x..x+7)
@@ -125,7 +120,7 @@ struct TcSmem {
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
-    float meanb[2];                                // BF16 / TF32 range offset of the tile in buffer b
+    float mean0;                                   // BF16 / TF32 range offset of the first tile
 };
 // Two CTAs share an SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
 static_assert(sizeof(TcSmem<false, kTallH>) + 1024 <= 228 * 1024 / 2, "BF16 tall tiles: two CTAs per SM");
@@ -705,17 +700,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (tile + (int)gridDim.x < ntiles) stage_input<TF, TOH>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
         cp_async_commit();
 
-        // ---- E: all rows for the first tile; for later ones the rows the expert warps did not build at the end of
-        // the previous tile ----
+        // ---- E: built here for the first tile; the expert warps build it for the later ones at the end of the
+        // previous tile ----
         const float *Ub = S.U[buf];
         if (k == 0) {
             if (warp == 0) {
                 const float m = region_mean<TOH>(Ub, lane);
-                if (lane == 0) S.meanb[0] = m;
+                if (lane == 0) S.mean0 = m;
             }
             __syncthreads();
+            build_e(S, Ub, S.mean0, 0, kUR<TOH>, tid, NTHR);
         }
-        build_e(S, Ub, S.meanb[buf], k == 0 ? 0 : kPreE<TOH>, kUR<TOH>, tid, NTHR);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -831,12 +826,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                     if (t == kNMT<TOH> - 1) done = true;
                 }
                 // every forward MMA of this tile is complete (each expert thread saw the last one), so E is free:
-                // the first rows of the next tile's E are built while the last adjoint and col2im finish
+                // the next tile's E is built while the last adjoint and col2im finish
                 if (done && tile + (int)gridDim.x < ntiles &&
                     mbar_wait(&S.bar[B_UREADY + (buf ^ 1)], ((k + 1) >> 1) & 1, abort_flag, status)) {
                     const float m = region_mean<TOH>(S.U[buf ^ 1], lane);
-                    if (tid == 0) S.meanb[buf ^ 1] = m;
-                    build_e(S, S.U[buf ^ 1], m, 0, kPreE<TOH>, tid, 128);
+                    build_e(S, S.U[buf ^ 1], m, 0, kUR<TOH>, tid, 128);
                 }
             } else {
                 for (int t = 0; t < kNMT<TOH>; ++t) {
