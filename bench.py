@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -131,12 +132,19 @@ class ClockSampler:
 KERNEL_SOURCES = {"foe_tc_step": ("foe_tc.cu", "foe_common.cuh"), "foe_f32_step": ("foe_f32.cu", "foe_common.cuh")}
 
 
+def code_only(text: str) -> str:
+    """CUDA/C++ source without its // comments, trailing blanks and blank lines (the sources here put no // inside
+    string literals), so that a comment edit does not count as a code change."""
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_sha(kernel_key: str) -> str:
-    """Hash of the sources of one kernel: an ncu figure is only used while they are unchanged."""
+    """Hash of the code of one kernel's sources: an ncu figure is only used while that code is unchanged."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel_key]:
-        with open(os.path.join(ROOT, "paper_1609_05722_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1609_05722_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

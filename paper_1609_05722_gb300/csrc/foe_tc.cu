@@ -25,6 +25,11 @@
 // over the first columns of R(g)'s stage, and the adjoint MMA reads its A operand from there, so Psi never passes
 // through shared memory; the stage is free again once that MMA is complete, Z(g) once the col2im has loaded it.  Expert and
 // col2im warps run decoupled, so the MMAs of later M-tiles overlap the epilogue of earlier ones.
+// CTAs are persistent (tiles c, c + gridDim.x, ...).  While a tile is computed, the next tile's input region is
+// copied in (cp.async, double-buffered; its completion arrives on an mbarrier), and once the tile's last forward
+// MMA is complete the expert warps build the next tile's E while the last adjoint and col2im finish; then all
+// warps run the output pass (vertical col2im, padding fold, iPiano step).  Launches are programmatically
+// dependent: a CTA sets up barriers and tensor memory before it waits for the previous step to complete.
 // Every mbarrier wait is bounded: on expiry the CTA records FOE_ETIMEOUT in *status, drains its MMAs,
 // frees its tensor memory and finishes without further waits.
 //
