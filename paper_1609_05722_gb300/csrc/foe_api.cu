@@ -121,7 +121,6 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
     float w[foe::kNF * foe::kKK] = {};
     for (int f = 0; f < c->nf; ++f)
         for (int t = 0; t < foe::kKK; ++t) w[f * foe::kKK + t] = c->kconv[f * foe::kKK + (foe::kKK - 1 - t)];
-    foe_status st = FOE_OK;
     auto fail = [&](foe_status s) {
         foe_destroy(c);
         return s;
@@ -139,7 +138,6 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(c->d_status, 0, sizeof(int))) || (e = foe::f32_setup()) || (e = foe::tc_setup()) || (e = foe::bwd_setup()))
         return fail(e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA);
-    (void)st;
     if (ensure_partials(c, 1024) != FOE_OK) return fail(FOE_ENOMEM);
     *out = c;
     return FOE_OK;
