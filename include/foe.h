@@ -58,8 +58,9 @@ typedef enum {
 typedef enum { FOE_MODEL_DIRECT = 0, FOE_MODEL_ANS_L2 = 1, FOE_MODEL_ANS_IDIV = 2, FOE_MODEL_AUTO = 3 } foe_model;
 
 /* Arithmetic of the 96 convolutions per iteration: FP32 on the FFMA units, or tcgen05 tensor cores with
- * TF32 or BF16 operands and FP32 accumulation.  State, data term and prox are always FP32 (the iterate is
- * held as an unevaluated FP32 pair hi + lo). */
+ * TF32 or BF16 operands and FP32 accumulation.  State, data term and prox are always FP32: the FP32 path
+ * holds the iterate as an unevaluated FP32 pair hi + lo, the tensor-core paths as plain FP32 (their BF16 /
+ * TF32 rounding of u and psi is orders of magnitude above the drift that the pair removes). */
 typedef enum { FOE_PREC_FP32 = 0, FOE_PREC_TF32 = 1, FOE_PREC_BF16 = 2 } foe_precision;
 
 typedef enum { FOE_BC_SYMMETRIC = 0, FOE_BC_ZERO = 1 } foe_bc;
