@@ -88,3 +88,19 @@ def test_small_graph_batch_against_oracle(ctx, prec):
             assert np.abs(x - ref).max() * 255.0 / s.peak <= 1e-4
         else:
             assert abs(O.psnr(x, clean, s.peak) - O.psnr(ref, clean, s.peak)) <= 0.02
+
+
+@pytest.mark.parametrize("prec", [F.FOE_PREC_BF16, F.FOE_PREC_TF32])
+def test_zero_padding_batch_equals_single_solves(ctx, prec):
+    # 8 images of 512 x 256: the batch has several tiles per CTA (the next tile's input region, zero rows
+    # included, is prefetched while a tile is computed), a single image at most one per CTA
+    specs = [synth.ImageSpec(512, 256, p, 20, 21 + j, 31 + j) for j, p in enumerate([1.0, 2.0, 4.0, 8.0] * 2)]
+    ys, xs, descs = upload(specs)
+    opts = dict(model=F.FOE_MODEL_AUTO, prec=prec, bc=F.FOE_BC_ZERO)
+    F.foe_denoise_batch(ctx, descs, F.SolveOpts(**opts))
+    torch.cuda.synchronize()
+    for j, s in enumerate(specs):
+        single = torch.zeros_like(xs[j])
+        F.foe_denoise(ctx, ys[j], single, s.H, s.W, descs[j]["ld"], s.peak, F.SolveOpts(iters=s.iters, **opts))
+        torch.cuda.synchronize()
+        assert torch.equal(single[:, :s.W], xs[j][:, :s.W]), j
