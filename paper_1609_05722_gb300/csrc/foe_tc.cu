@@ -502,8 +502,8 @@ __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, const TcSmem<
 }
 
 // Issue the asynchronous copies of a tile's input region into buffer b and record its geometry there (all
-// threads; the caller commits the cp.async group).  Positions outside the padded image are zero-filled with plain
-// stores.
+// threads; the caller commits the cp.async group).  Positions outside the padded image are zero-filled by the copy
+// engine too, and each thread then arrives on the buffer's mbarrier once its copies have landed.
 template <bool TF, int TOH>
 __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH> &S, int tile, int b, int tid, int warp,
                                             int lane)
