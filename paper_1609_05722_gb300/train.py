@@ -79,6 +79,41 @@ class FoEImplicitLoss(torch.autograd.Function):
         return g * dk, g * dla, None, None, None, None, None, None, None, None, None
 
 
+class DataParallelLoss(torch.autograd.Function):
+    """Data-parallel training over ranks that each hold a share of the training pairs (the loss of Sec. 3.2 is a
+    sum over samples, so the batch splits freely).
+
+    loss = DataParallelLoss.apply(filters, log_alpha, local_loss_fn, dist)
+
+    local_loss_fn(filters, log_alpha) is this rank's loss (for instance FoEUnrolledLoss or FoEImplicitLoss over its
+    images).  The forward pass evaluates it and its gradients, then sums the loss and the gradients (nf x 49 filter
+    coefficients and nf log-weights) over the ranks with one all-reduce of one FP64 vector; every rank returns the
+    whole batch's loss, and backward gives the whole batch's gradients, so ranks that start from the same
+    parameters take the same optimizer steps (lbfgs_train runs unchanged on every rank)."""
+
+    @staticmethod
+    def forward(ctx, filters, log_alpha, local_loss_fn, dist, group=None):
+        with torch.enable_grad():
+            k = filters.detach().requires_grad_(True)
+            la = log_alpha.detach().requires_grad_(True)
+            local = local_loss_fn(k, la)
+            gk, gla = torch.autograd.grad(local, (k, la))
+        # NCCL reduces device tensors, gloo host tensors
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else "cpu"
+        v = torch.cat([local.detach().reshape(1).double().to(dev), gk.detach().reshape(-1).double().to(dev),
+                       gla.detach().reshape(-1).double().to(dev)])
+        dist.all_reduce(v, group=group)
+        nk = gk.numel()
+        ctx.save_for_backward(v[1:1 + nk].view_as(gk).to(filters.device, filters.dtype),
+                              v[1 + nk:].view_as(gla).to(log_alpha.device, log_alpha.dtype))
+        return v[0].to(device=filters.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        gk, gla = ctx.saved_tensors
+        return grad_out.to(gk.dtype) * gk, grad_out.to(gla.dtype) * gla, None, None, None
+
+
 def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1e-5, history: int = 10,
                 on_step=None):
     """Algorithm 1 (Sec. 2.5): L-BFGS over the filters and log-weights of the prior.
