@@ -10,6 +10,8 @@ scales the stored gradients.  tau is a constant of the solve (no gradient flows 
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import torch
 
@@ -115,7 +117,7 @@ class DataParallelLoss(torch.autograd.Function):
 
 
 def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1e-5, history: int = 10,
-                on_step=None):
+                on_step=None, checkpoint: str | None = None):
     """Algorithm 1 (Sec. 2.5): L-BFGS over the filters and log-weights of the prior.
 
     loss_fn(filters, log_alpha) returns the training loss as a differentiable scalar tensor (for instance
@@ -123,7 +125,12 @@ def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1
     strong-Wolfe line search; training stops when the relative change of the loss falls below tol, after max_iter
     iterations, or when a step fails to decrease the loss (the three criteria of the paper's training).
     on_step(iteration, loss), if given, is called after every step.  Returns (filters, log_alpha, losses, reason),
-    losses[0] being the initial loss."""
+    losses[0] being the initial loss.
+
+    checkpoint, if given, is a file path: after every step the training state (parameters, the L-BFGS history and
+    line-search state, the losses so far) is written there (atomically, with torch.save), and a call that finds the
+    file resumes from it, the filters / log_alpha arguments then serving only as templates; max_iter counts the
+    steps of the whole run.  A resumed run takes the same steps as an uninterrupted one."""
     k = filters.detach().clone().requires_grad_(True)
     la = log_alpha.detach().clone().requires_grad_(True)
     # one L-BFGS iteration per step; the line search may take up to 20 evaluations within it
@@ -136,15 +143,29 @@ def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1
         L.backward()
         return L
 
-    with torch.no_grad():
-        losses = [float(loss_fn(k, la))]
+    start = 0
+    if checkpoint is not None and os.path.exists(checkpoint):
+        st = torch.load(checkpoint, weights_only=False)
+        with torch.no_grad():
+            k.copy_(st["filters"])
+            la.copy_(st["log_alpha"])
+        opt.load_state_dict(st["optimizer"])
+        losses, start = list(st["losses"]), int(st["iteration"])
+    else:
+        with torch.no_grad():
+            losses = [float(loss_fn(k, la))]
     reason = "max_iter"
-    for it in range(max_iter):
+    for it in range(start, max_iter):
         opt.step(closure)
         with torch.no_grad():
             L = float(loss_fn(k, la))
         prev = losses[-1]
         losses.append(L)
+        if checkpoint is not None:
+            tmp = f"{checkpoint}.tmp{os.getpid()}"
+            torch.save({"filters": k.detach().clone(), "log_alpha": la.detach().clone(),
+                        "optimizer": opt.state_dict(), "losses": losses, "iteration": it + 1}, tmp)
+            os.replace(tmp, checkpoint)
         if on_step is not None:
             on_step(it + 1, L)
         if not L < prev:

@@ -77,3 +77,17 @@ def test_lbfgs_stops_when_no_step_decreases_the_loss():
     _, _, losses, reason = lbfgs_train(Flat.apply, torch.zeros(6, 7, 7, dtype=torch.float64),
                                        torch.zeros(6, dtype=torch.float64), max_iter=10, tol=0.0)
     assert reason == "no_decrease" and len(losses) == 2
+
+
+def test_lbfgs_resumes_from_a_checkpoint_bit_for_bit(problem, tmp_path):
+    k, a, clean, noisy = problem
+    k0, la0 = torch.from_numpy(k).double(), torch.from_numpy(np.log(a)).double()
+    straight = lbfgs_train(make_loss(clean, noisy, []), k0, la0, max_iter=4, tol=0.0)
+    ck = str(tmp_path / "train.pt")
+    first = lbfgs_train(make_loss(clean, noisy, []), k0, la0, max_iter=2, tol=0.0, checkpoint=ck)
+    assert len(first[2]) == 3
+    # a fresh process would start from the same templates; the file holds the parameters and the L-BFGS history
+    resumed = lbfgs_train(make_loss(clean, noisy, []), torch.zeros_like(k0), torch.zeros_like(la0), max_iter=4,
+                          tol=0.0, checkpoint=ck)
+    assert torch.equal(resumed[0], straight[0]) and torch.equal(resumed[1], straight[1])
+    assert resumed[2] == straight[2] and resumed[3] == straight[3]
