@@ -110,3 +110,35 @@ def test_strip_partition():
         domain.strip_rows(11, 2, 0)
     with pytest.raises(ValueError):
         domain.strip_rows(40, 2, 2)
+
+
+def _dying_worker(rank, world, port, q):
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)  # this rank leaves between steps, before its first exchange
+    d = torch.zeros((H, W), dtype=torch.float64)
+    e0, e1 = domain.extended_rows(H, world, rank)
+    t0 = time.time()
+    try:
+        domain.solve_strip(lambda d_, u, up: u, d[e0:e1], d[e0:e1], 3, H, world, rank, dist)
+        q.put((rank, "finished", time.time() - t0))
+    except Exception as e:  # the exchange with the lost neighbour fails instead of waiting forever
+        q.put((rank, type(e).__name__, time.time() - t0))
+    os._exit(0)
+
+
+def test_a_lost_neighbour_ends_the_exchange_with_an_error():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, what, elapsed = q.get(timeout=120)
+    for p in procs:
+        p.join(60)
+    assert rank == 0 and what != "finished" and elapsed < 60
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
