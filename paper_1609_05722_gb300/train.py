@@ -130,7 +130,10 @@ def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1
     checkpoint, if given, is a file path: after every step the training state (parameters, the L-BFGS history and
     line-search state, the losses so far) is written there (atomically, with torch.save), and a call that finds the
     file resumes from it, the filters / log_alpha arguments then serving only as templates; max_iter counts the
-    steps of the whole run.  A resumed run takes the same steps as an uninterrupted one."""
+    steps of the whole run.  A resumed run takes the same steps as an uninterrupted one.  The stopping decision of
+    a step is taken before its checkpoint is written and is stored in it, so a run resumed from the checkpoint of a
+    run that had already stopped returns at once with the stored result; a checkpoint without a stored decision has
+    the criteria re-checked on its last two losses."""
     k = filters.detach().clone().requires_grad_(True)
     la = log_alpha.detach().clone().requires_grad_(True)
     # one L-BFGS iteration per step; the line search may take up to 20 evaluations within it
@@ -151,6 +154,11 @@ def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1
             la.copy_(st["log_alpha"])
         opt.load_state_dict(st["optimizer"])
         losses, start = list(st["losses"]), int(st["iteration"])
+        stopped = st.get("reason")
+        if stopped is None and len(losses) >= 2:
+            stopped = _stop_reason(losses[-2], losses[-1], tol)
+        if stopped is not None:
+            return k.detach(), la.detach(), losses, stopped
     else:
         with torch.no_grad():
             losses = [float(loss_fn(k, la))]
@@ -161,17 +169,25 @@ def lbfgs_train(loss_fn, filters, log_alpha, max_iter: int = 500, tol: float = 1
             L = float(loss_fn(k, la))
         prev = losses[-1]
         losses.append(L)
+        stop = _stop_reason(prev, L, tol)
         if checkpoint is not None:
             tmp = f"{checkpoint}.tmp{os.getpid()}"
             torch.save({"filters": k.detach().clone(), "log_alpha": la.detach().clone(),
-                        "optimizer": opt.state_dict(), "losses": losses, "iteration": it + 1}, tmp)
+                        "optimizer": opt.state_dict(), "losses": losses, "iteration": it + 1, "reason": stop}, tmp)
             os.replace(tmp, checkpoint)
         if on_step is not None:
             on_step(it + 1, L)
-        if not L < prev:
-            reason = "no_decrease"
-            break
-        if abs(prev - L) <= tol * abs(prev):
-            reason = "tol"
+        if stop is not None:
+            reason = stop
             break
     return k.detach(), la.detach(), losses, reason
+
+
+def _stop_reason(prev: float, L: float, tol: float):
+    """The stopping rules of the training loop after a step from loss prev to loss L: a step that does not decrease
+    the loss, or a relative change of at most tol; None to go on."""
+    if not L < prev:
+        return "no_decrease"
+    if abs(prev - L) <= tol * abs(prev):
+        return "tol"
+    return None

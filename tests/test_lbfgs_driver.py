@@ -91,3 +91,26 @@ def test_lbfgs_resumes_from_a_checkpoint_bit_for_bit(problem, tmp_path):
                           tol=0.0, checkpoint=ck)
     assert torch.equal(resumed[0], straight[0]) and torch.equal(resumed[1], straight[1])
     assert resumed[2] == straight[2] and resumed[3] == straight[3]
+
+
+def test_lbfgs_resumed_after_it_stopped_returns_the_stored_result(problem, tmp_path):
+    k, a, clean, noisy = problem
+    k0, la0 = torch.from_numpy(k).double(), torch.from_numpy(np.log(a)).double()
+    ck = str(tmp_path / "stopped.pt")
+    done = lbfgs_train(make_loss(clean, noisy, []), k0, la0, max_iter=50, tol=5e-2, checkpoint=ck)
+    assert done[3] == "tol"
+    # resuming the finished run takes no step and evaluates no loss
+    calls = []
+    again = lbfgs_train(make_loss(clean, noisy, calls), torch.zeros_like(k0), torch.zeros_like(la0), max_iter=50,
+                        tol=5e-2, checkpoint=ck)
+    assert calls == []
+    assert torch.equal(again[0], done[0]) and torch.equal(again[1], done[1])
+    assert again[2] == done[2] and again[3] == "tol"
+    # a checkpoint that holds no stopping decision has the criteria re-checked on its last two losses
+    st = torch.load(ck, weights_only=False)
+    del st["reason"]
+    torch.save(st, ck)
+    calls = []
+    old = lbfgs_train(make_loss(clean, noisy, calls), torch.zeros_like(k0), torch.zeros_like(la0), max_iter=50,
+                      tol=5e-2, checkpoint=ck)
+    assert calls == [] and old[3] == "tol" and old[2] == done[2]
