@@ -176,13 +176,13 @@ FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, in
 FOE_API foe_status foe_denoise_binned(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                                       const foe_solve_opts *opts, void *stream, foe_report *rep);
 
-/* foe_denoise for callers that cannot allocate device memory at the time of the call: code that runs
- * while a CUDA graph is being captured (cudaMalloc is not permitted under global capture), code whose
- * device memory is owned entirely by another allocator (a framework's caching allocator or a fixed
- * arena), and real-time loops that cannot afford cudaMalloc's implicit device synchronisation.  It
- * computes exactly what foe_denoise computes, but its workspace is a fixed 20 MiB device array inside
- * the library instead of context memory; it never calls cudaMalloc, cudaFree or any allocating
- * routine.  The paper has no counterpart of this entry point.
+/* foe_denoise for callers that cannot allocate device memory at the time of the call: code whose device
+ * memory is owned entirely by another allocator (a framework's caching allocator or a fixed arena sized at
+ * start-up, where a cudaMalloc from here would bypass its accounting or fail once the arena holds the
+ * device), and real-time loops that cannot afford the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  It computes exactly what foe_denoise computes, but its workspace is a fixed 20 MiB device
+ * array inside the library instead of context memory; it never calls cudaMalloc, cudaFree or any
+ * allocating routine.  The paper has no counterpart of this entry point.
  *   - Size limit: H * ld <= 1048576 floats (e.g. 1024 x 1024); larger images return FOE_EINVAL with a
  *     message, before any device work.
  *   - The array is shared by every call in the process on a device and keeps the last call's contents;
@@ -191,6 +191,11 @@ FOE_API foe_status foe_denoise_binned(foe_ctx *ctx, const float *y, float *x, in
  *     that device current; make that first call before any stream capture begins.
  *   - No report and no profiling: nothing is synchronised.  The context (created earlier, when
  *     allocation was possible) supplies the filters.
+ *   - A device-side wait of the tensor-core kernel that expired earlier in this context (FOE_ETIMEOUT,
+ *     sticky until read) makes every later tensor-core step launch of the context return at once.  This
+ *     call cannot read that status without synchronising, so on the BF16 / TF32 paths its output map then
+ *     fills x with NaN instead of a stale iterate; call foe_device_status (which reads and clears the
+ *     status) after a solve whose result matters.
  * Arguments and the other errors are those of foe_denoise. */
 FOE_API foe_status foe_denoise_static(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                                       const foe_solve_opts *opts, void *stream);

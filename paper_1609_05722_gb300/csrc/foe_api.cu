@@ -699,7 +699,10 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
         if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
     }
     const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
-    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, nullptr, s));
+    // no status is read back here (nothing is synchronised): on the tensor-core paths, whose step launches do
+    // nothing while the context's device status is set, an expired device wait shows as a NaN output
+    const int *guard = o->prec == FOE_PREC_FP32 ? nullptr : c->d_status;
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, nullptr, s, guard));
     return FOE_OK;
 }
 

@@ -263,11 +263,17 @@ __device__ __forceinline__ double inv_anscombe(double z)
 
 // Output map: x = I_C(max(u, sqrt(3/2))) (Eq. invAns) for the Anscombe models, x = u for the direct one.
 // Output map; counts the non-finite outputs into *nonfinite when it is given (a NaN / Inf sentinel).
+// status (nullable): the context's sticky device status; while it is set the solve's step launches did nothing,
+// so the output is NaN rather than a stale iterate (for callers that return without reading the status)
 __global__ void k_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x,
-                         int *nonfinite)
+                         int *nonfinite, const int *status)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (c >= W || r >= H) return;
+    if (status && *(const volatile int *)status != 0) {
+        x[(size_t)r * xld + c] = __int_as_float(0x7fc00000);
+        return;
+    }
     const size_t i = (size_t)r * ld + c;
     const double u = (double)uh[i] + (ul ? (double)ul[i] : 0.0);
     const float v = model == kDirect ? (float)u : (float)inv_anscombe(u);
@@ -337,10 +343,10 @@ cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model
 }
 
 cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x, int *nonfinite,
-                          cudaStream_t s)
+                          cudaStream_t s, const int *status)
 {
     dim3 g((W + 127) / 128, H);
-    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x, nonfinite);
+    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x, nonfinite, status);
     return cudaGetLastError();
 }
 

@@ -34,9 +34,10 @@ cudaError_t launch_copy(const float *src, float *dst, long n, cudaStream_t s);
 
 cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model, float zero_c, float *d, float *uh,
                         float *ul, float *delta, cudaStream_t s);
-// x = the output map of the iterate; *nonfinite (nullable) += the number of non-finite outputs
+// x = the output map of the iterate; *nonfinite (nullable) += the number of non-finite outputs; x = NaN while
+// *status (nullable: not checked) is non-zero
 cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x, int *nonfinite,
-                          cudaStream_t s);
+                          cudaStream_t s, const int *status = nullptr);
 cudaError_t launch_anscombe(const float *y, float *v, long n, cudaStream_t s);
 cudaError_t launch_inverse(const float *z, float *x, long n, cudaStream_t s);
 cudaError_t launch_reduce(const double *p, int n, double *out, cudaStream_t s);
