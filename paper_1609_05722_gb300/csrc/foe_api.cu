@@ -127,12 +127,15 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
     };
     const std::vector<uint16_t> ops = tc_operands(w, c->alpha);
     const std::vector<uint32_t> ops32 = tc_operands_tf32(w, c->alpha);
+    const std::vector<uint16_t> pops = pair_operands(w, c->alpha);
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_wts, sizeof(w))) || (e = cudaMalloc(&c->d_alpha, sizeof(c->alpha))) ||
         (e = cudaMalloc(&c->d_tcops, ops.size() * sizeof(uint16_t))) ||
         (e = cudaMemcpy(c->d_tcops, ops.data(), ops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice)) ||
         (e = cudaMalloc(&c->d_tcops32, ops32.size() * sizeof(uint32_t))) ||
         (e = cudaMemcpy(c->d_tcops32, ops32.data(), ops32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) ||
+        (e = cudaMalloc(&c->d_pairops, pops.size() * sizeof(uint16_t))) ||
+        (e = cudaMemcpy(c->d_pairops, pops.data(), pops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice)) ||
         (e = cudaMalloc(&c->d_energy, sizeof(double))) || (e = cudaMalloc(&c->d_status, sizeof(int))) || (e = cudaMalloc(&c->d_nonfinite, sizeof(int))) ||
         (e = cudaMemcpy(c->d_wts, w, sizeof(w), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
@@ -151,6 +154,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_alpha);
     cudaFree(c->d_tcops);
     cudaFree(c->d_tcops32);
+    cudaFree(c->d_pairops);
     cudaFree(c->d_energy);
     cudaFree(c->d_status);
     cudaFree(c->d_nonfinite);

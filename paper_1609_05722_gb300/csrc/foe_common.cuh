@@ -55,6 +55,7 @@ struct LaunchArgs {
     double *partials;          // kEnergy: one FP64 partial per tile
     const void *tcops;         // tensor-core operand images (bf16): forward filters, then adjoint filters
     const void *tcops32;       // the same images in tf32
+    const void *pairops;       // operand images of the pixel-pair kernel (bf16)
     int tile_prefix[kMaxBatch + 1];
     ImgDesc img[kMaxBatch];
 };

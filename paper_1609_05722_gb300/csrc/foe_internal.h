@@ -28,6 +28,7 @@ struct foe_ctx {
     float *d_alpha = nullptr;               // device [48]
     void *d_tcops = nullptr;                // device, bf16 operand images of the tensor-core kernel (12 KB)
     void *d_tcops32 = nullptr;              // device, the same in tf32 (24 KB)
+    void *d_pairops = nullptr;              // device, bf16 operand images of the pixel-pair kernel (24 KB)
     void *ws = nullptr;
     size_t ws_bytes = 0;
     float *d_bin = nullptr;                 // foe_denoise_binned: the bin image and its estimate
@@ -137,6 +138,37 @@ inline std::vector<uint16_t> tc_operands(const float *w, const float *alpha)
             for (int e = 0; e < 8; ++e) {
                 const int f = 8 * g + e, a = n / 8, b = n % 8;
                 adj[(g * 64 + n) * 8 + e] = (a < 7 && b < 7) ? f32_to_bf16(2.0f * alpha[f] * w[f * foe::kKK + a * 7 + b]) : 0;
+            }
+    return out;
+}
+
+// bf16 operand images of the pixel-pair kernel (foe_pair.cu), from correlation weights w[48][49] and alpha.  Within
+// each group of four filters the tensor-memory (and K) order is f0, f2, f1, f3 (sigma = {0, 2, 1, 3}), so that
+// one reciprocal serves the pair (f0, f1) and the pair (f2, f3) with aligned f32x2 operands.
+//   forward B  [tap row a (8)][n = 48 s + e (96)][column c (8)] = w_f(a, c - s), f = 4 (e / 4) + sigma(e % 4)
+//              (s: pixel of the pair; 0 unless a < 7 and 0 <= c - s < 7)
+//   adjoint B  [K chunk h (12)][n' = 8 a + slot (64)][K value e8 (8)] = 2 alpha_f w_f(a, c - s) with s = h / 6,
+//              e = 8 (h % 6) + e8, f as above, c = {3, 4, 1, 2, 5, 6, 7, 0}[slot] (the column offset 2j + c - 3
+//              of the output that pair j feeds; 0 unless a < 7 and 0 <= c - s < 7)
+inline std::vector<uint16_t> pair_operands(const float *w, const float *alpha)
+{
+    static const int sigma[4] = {0, 2, 1, 3};
+    static const int slot_c[8] = {3, 4, 1, 2, 5, 6, 7, 0};
+    auto filt = [&](int e) { return 4 * (e / 4) + sigma[e % 4]; };
+    std::vector<uint16_t> out(8 * 96 * 8 + 12 * 64 * 8, 0);
+    for (int a = 0; a < 8; ++a)
+        for (int n = 0; n < 96; ++n)
+            for (int c = 0; c < 8; ++c) {
+                const int s = n / 48, f = filt(n % 48), b = c - s;
+                out[(a * 96 + n) * 8 + c] = (a < 7 && b >= 0 && b < 7) ? f32_to_bf16(w[f * foe::kKK + a * 7 + b]) : 0;
+            }
+    uint16_t *adj = out.data() + 8 * 96 * 8;
+    for (int h = 0; h < 12; ++h)
+        for (int n = 0; n < 64; ++n)
+            for (int e8 = 0; e8 < 8; ++e8) {
+                const int s = h / 6, f = filt(8 * (h % 6) + e8), a = n / 8, b = slot_c[n % 8] - s;
+                adj[(h * 64 + n) * 8 + e8] =
+                    (a < 7 && b >= 0 && b < 7) ? f32_to_bf16(2.0f * alpha[f] * w[f * foe::kKK + a * 7 + b]) : 0;
             }
     return out;
 }
@@ -254,7 +286,7 @@ inline void tile_dims(int prec, int H, int &th, int &tw)
 {
     if (prec == FOE_PREC_BF16 || prec == FOE_PREC_TF32) {
         th = foe::tc_tile_h(prec == FOE_PREC_TF32, H);
-        tw = foe::tc_tile_w();
+        tw = foe::tc_tile_w(th);
     } else {
         th = tw = foe::f32_tile();
     }
@@ -274,6 +306,7 @@ inline void args_begin(foe_ctx *c, int bc)
     A.partials = c->d_partials;
     A.tcops = c->d_tcops;
     A.tcops32 = c->d_tcops32;
+    A.pairops = c->d_pairops;
     A.tile_prefix[0] = 0;
 }
 

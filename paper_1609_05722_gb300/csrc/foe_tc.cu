@@ -43,10 +43,13 @@
 
 #include "foe_common.cuh"
 #include "foe_kernels.h"
+#include "foe_ptx.cuh"
 
 namespace foe {
 
 namespace {
+
+using namespace ptx;
 
 constexpr int TO = 26;                 // output tile width
 constexpr int RS = TO + 6;             // response region width = 32 = warp width
@@ -60,7 +63,7 @@ constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 us
 // depend on the batch.  Two CTAs still fit an SM with the tall tiles because the horizontal col2im sums are kept in
 // FP16 on the BF16 path (their magnitude stays far below its range, and its 11-bit significand is finer than the
 // BF16 rounding of u and psi); TF32 keeps FP32 sums and its ~4x smaller error.
-constexpr int kTallH = 58, kShortH = 26;
+constexpr int kShortH = 26;
 template <bool TF>
 struct HsType {
     using T = __half;
@@ -82,8 +85,6 @@ constexpr int NWARP = NEPI + 2;
 constexpr int NTHR = 32 * NWARP;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t Z_COL0 = 128;       // R(g) at 64 (g & 1) (48 columns), Z(g) at 128 + 64 (g & 1) (64 columns)
-constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
-constexpr uint32_t kSuspendHintNs = 100000;           // a waiting thread may sleep up to 0.1 ms per try
 
 // Operand images in shared memory.  BF16: 16-byte entries of 8 values.  TF32: 16-byte entries of 4 values,
 // so every 8-value K-chunk of the BF16 layout becomes two chunks (E is split into E[0] = u(x..x+3) and
@@ -119,7 +120,7 @@ struct TcSmem {
     float U[2][kUR<TOH> * UC];                     // fp32 input region (this tile / the next one, copied in meanwhile)
     float O[2][TO * TOH];                          // output-pass operands delta, d (staged after the previous tile)
     int srow[2][kUR<TOH>], scol[2][RS + 7];        // source row / column of each region row / column (-1: zero)
-    int geo[2][4];                                 // image, oy0, ox0, write limit xe of the tile in buffer b
+    int geo[2][5];                                 // image, oy0, ox0, column write range [xs, xe) of the tile in buffer b
     int tprefix[kMaxBatch + 1];                    // the launch's tile prefix, and per image: tiles per row, H, W
     int timg[kMaxBatch][3];
     uint64_t bar[NBAR];
@@ -128,271 +129,14 @@ struct TcSmem {
     float mean0;                                   // BF16 / TF32 range offset of the first tile
 };
 // Two CTAs share an SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-static_assert(sizeof(TcSmem<false, kTallH>) + 1024 <= 228 * 1024 / 2, "BF16 tall tiles: two CTAs per SM");
 static_assert(sizeof(TcSmem<false, kShortH>) + 1024 <= 228 * 1024 / 2, "BF16 tiles: two CTAs per SM");
 static_assert(sizeof(TcSmem<true, kShortH>) + 1024 <= 228 * 1024 / 2, "TF32 tiles: two CTAs per SM");
 // Wf and Wa are filled by one bulk copy of the packed operand images
-using SmemBf16Tall = TcSmem<false, kTallH>;
 using SmemBf16 = TcSmem<false, kShortH>;
 using SmemTf32 = TcSmem<true, kShortH>;
-static_assert(offsetof(SmemBf16Tall, Wa) == offsetof(SmemBf16Tall, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
 static_assert(offsetof(SmemBf16, Wa) == offsetof(SmemBf16, Wf) + sizeof(uint4) * TcOps<false>::WF, "");
 static_assert(offsetof(SmemTf32, Wa) == offsetof(SmemTf32, Wf) + sizeof(uint4) * TcOps<true>::WF, "");
-static_assert(offsetof(SmemBf16Tall, U) % 8 == 0 && offsetof(SmemBf16, U) % 8 == 0 && offsetof(SmemTf32, U) % 8 == 0 && UC % 2 == 0 && UC >= 40, "");
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false if the CTA gave up.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
-{
-    const long long t0 = clock64();
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 31u) == 31u) {
-            if (*abort_flag) return false;
-            if (clock64() - t0 > kTimeoutCycles) {
-                *abort_flag = 1;
-                atomicExch(status, (int)5 /* FOE_ETIMEOUT */);
-                return false;
-            }
-        }
-    }
-}
-
-// Fast path: one probe (which may suspend the thread until the phase completes); otherwise the bounded loop.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, abort_flag, status);
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    // K-major, no swizzle: core matrices of 8 rows x 16 B; lbo = next core matrix along K,
-    // sbo = next group of 8 rows; bits 46-47 = descriptor version 1.  The start address (bits 0-13,
-    // in 16-byte units) of every operand used here stays below 2^14, so an offset in 16-byte units can
-    // be added to a descriptor directly.
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
-{
-    // D FP32 (bit 4), A BF16 (bits 7-9 = 1), B BF16 (bits 10-12 = 1), both K-major,
-    // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N)
-{
-    // D FP32 (bit 4), A TF32 (bits 7-9 = 2), B TF32 (bits 10-12 = 2), both K-major.
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// Bounded wait with a warp-uniform result (every lane waits; the warp gives up if any lane gave up).
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status)
-{
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag, status));
-}
-
-// Warp-uniform issue: the whole warp executes these, one elected lane (the lowest, lane 0) issues.
-template <bool TF>
-__device__ __forceinline__ void mma_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if (TF)
-        asm volatile(
-            "{\n\t.reg .pred p, e;\n\t"
-            "elect.sync _|e, 0xffffffff;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p, e;\n\t"
-            "elect.sync _|e, 0xffffffff;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-}
-
-template <bool TF>
-__device__ __forceinline__ void mma_ta_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if (TF)
-        asm volatile(
-            "{\n\t.reg .pred p, e;\n\t"
-            "elect.sync _|e, 0xffffffff;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p, e;\n\t"
-            "elect.sync _|e, 0xffffffff;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-}
-
-__device__ __forceinline__ void commit_elect(uint64_t *bar)
-{
-    asm volatile(
-        "{\n\t.reg .pred e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x)
-{
-    uint32_t d;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(d) : "f"(x));
-    return d;
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr)
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
-{
-    tmem_ld16(taddr, v);
-    tmem_ld16(taddr + 16, v + 16);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// Zero fill through the copy engine (no bytes read): every store to the input region is then a cp.async, whose
-// completion the region's mbarrier tracks
-__device__ __forceinline__ void cp_async_zero(void *dst, const void *any, int bytes)
-{
-    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 0;" ::"r"(smem_u32(dst)), "l"(any) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 0;" ::"r"(smem_u32(dst)), "l"(any) : "memory");
-}
-
-// arrive on an mbarrier once all of this thread's earlier cp.async copies have landed
-__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// bulk global -> shared copy completing on an mbarrier (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
-{
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-    return d;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-                     taddr),
-                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-                 "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *v)
-{
-    tmem_st16(taddr, v);
-    tmem_st16(taddr + 16, v + 16);
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+static_assert(offsetof(SmemBf16, U) % 8 == 0 && offsetof(SmemTf32, U) % 8 == 0 && UC % 2 == 0 && UC >= 40, "");
 
 // psi = r / (1 + r^2) for a pair of responses with packed f32x2 arithmetic, rounded to a bf16x2 word
 __device__ __forceinline__ uint32_t psi_bf16x2(float r0, float r1)
@@ -408,33 +152,6 @@ __device__ __forceinline__ uint32_t psi_bf16x2(float r0, float r1)
     float p0, p1;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(p0), "=f"(p1) : "l"(p));
     return pack_bf16x2(p0, p1);
-}
-
-// iPiano step (Eq. iPianoupdate) with the proximal map of the data term, on a plain FP32 iterate: the tensor-core
-// paths round u and psi to BF16 / TF32, which dominates the error, so the compensated (hi + lo) state of the FP32
-// path is not kept here (u_lo is neither read nor written).  The I-divergence prox (t + sqrt(t^2 + 4cd)) / 2,
-// t = u~ - c, is evaluated as 2cd / (sqrt(t^2 + 4cd) - t) for t < 0, which avoids the cancellation.
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void ipiano_update_f32(float g, float uh, float delta, float d, int model,
-                                                  const StepConsts &sc, float &nh, float &ndelta)
-{
-    const float ut = uh + fmaf(sc.gamma, delta, -sc.tau * g);
-    float p;
-    if (model == kAnsL2) {
-        p = fmaf(sc.a1_hi, ut, sc.a2_hi * d);
-    } else {
-        const float c = sc.c_hi, t = ut - c, cd4 = 4.0f * c * d;
-        const float sq = sqrt_approx(fmaf(t, t, cd4));
-        p = t >= 0.0f ? 0.5f * (t + sq) : __fdividef(0.5f * cd4, sq - t);
-    }
-    nh = p;
-    ndelta = p - uh;
 }
 
 __device__ __forceinline__ float hs_val(float v) { return v; }
@@ -469,17 +186,19 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF, TOH> &S, int qy, int
     return g;
 }
 
-// Image, origin and column write limit of a tile.  The horizontal col2im of a response row is formed across
-// the 32 lanes of a warp, so its sums exist only at region columns 0..31.  The padding fold of a pixel within 3
-// columns of the right border needs the sum at its reflection (up to column W + 2), which lies inside the region
-// only if the tile reaches that border: the last tile of a row is therefore placed flush right (origin W - 26)
-// and the tile before it writes only the columns left of that origin.  Rows need no such rule: the vertical part
-// of the col2im reads response rows, and the rows that a reflection asks for that lie in the image are always
-// within 3 rows of the output row.  The lookup reads the launch's tile table from its copy in shared memory,
-// made at the start of the kernel: parameter-space loads here sat on the staging thread's dependent chain.
+// Image, origin and column write range [xs, xe) of a tile.  The horizontal col2im of a response row is formed
+// across the 32 lanes of a warp, so its sums exist only at region columns 0..31.  The padding fold of a pixel
+// within 3 columns of the right border needs the sum at its reflection (up to column W + 2), which lies inside the
+// region only if the tile reaches that border: the last tile of a row is therefore placed flush right (origin
+// W - 26) and the tile before it writes only the columns left of max(W - 26, 3).  The bound 3 keeps the columns
+// within 3 of the left border in the first tile (origin 0), whose region holds their reflections, when the flush
+// tile starts at column 1 or 2 (W = 27, 28).  Rows need no such rule: the vertical part of the col2im reads
+// response rows, and the rows that a reflection asks for that lie in the image are always within 3 rows of the
+// output row.  The lookup reads the launch's tile table from its copy in shared memory, made at the start of the
+// kernel: parameter-space loads here sat on the staging thread's dependent chain.
 template <bool TF, int TOH>
 __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int tile, int &im,
-                                              int &oy0, int &ox0, int &xe)
+                                              int &oy0, int &ox0, int &xe, int &xs)
 {
     int lo = 0, hi = A.nimg - 1;
     while (lo < hi) {
@@ -494,10 +213,12 @@ __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, const TcSmem<
     oy0 = (lt / tiles_x) * TOH;
     ox0 = tx * TO;
     xe = min(ox0 + TO, W);
+    xs = ox0;
     if (W > TO) {
-        const int last = W - TO;
+        const int last = W - TO, split = max(last, 3);
         ox0 = min(ox0, last);
-        xe = tx + 1 < tiles_x ? min(xe, last) : W;
+        xs = tx + 1 < tiles_x ? ox0 : split;
+        xe = tx + 1 < tiles_x ? min(xe, split) : W;
     }
 }
 
@@ -508,7 +229,7 @@ template <bool TF, int TOH>
 __device__ __forceinline__ void stage_input(const LaunchArgs &A, TcSmem<TF, TOH> &S, int tile, int b, int tid, int warp,
                                             int lane)
 {
-    if (tid == 0) tile_geometry(A, S, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3]);
+    if (tid == 0) tile_geometry(A, S, tile, S.geo[b][0], S.geo[b][1], S.geo[b][2], S.geo[b][3], S.geo[b][4]);
     __syncthreads();
     const int im = S.geo[b][0], oy0 = S.geo[b][1], ox0 = S.geo[b][2];
     const ImgDesc &D = A.img[im];
@@ -692,7 +413,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int buf = k & 1;
-        const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3];
+        const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3], xs = S.geo[buf][4];
         const ImgDesc &D = A.img[im];
         const int H = D.H, W = D.W, ld = D.ld;
 
@@ -904,7 +625,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 const int r = warp + k2 * NWARP, yo = 3 + r, gy = oy0 + r;
-                ok_r[k2] = r < TOH && gy < H && gx < xe;
+                ok_r[k2] = r < TOH && gy < H && gx < xe && gx >= xs;
                 g[k2] = 0.0f;
                 uh[k2] = 0.0f;
                 if (ok_r[k2]) {
@@ -997,53 +718,18 @@ cudaError_t tc_attr()
 
 }  // namespace
 
-int tc_tile_h(bool tf32, int H) { return !tf32 && H >= 4 * kTallH ? kTallH : kShortH; }
-int tc_tile_w() { return TO; }
-size_t tc_smem_bytes() { return smem_request<false, kTallH>(); }
+int tc_tile_h(bool tf32, int H) { return !tf32 && H >= pair_min_rows() ? pair_tile() : kShortH; }
+int tc_tile_w(int tile_h) { return tile_h == pair_tile() ? pair_tile() : TO; }
 
 cudaError_t tc_setup()
 {
     cudaError_t e;
-    if ((e = tc_attr<kStep, false, kTallH>())) return e;
-    if ((e = tc_attr<kGrad, false, kTallH>())) return e;
     if ((e = tc_attr<kStep, false, kShortH>())) return e;
     if ((e = tc_attr<kGrad, false, kShortH>())) return e;
     if ((e = tc_attr<kStep, true, kShortH>())) return e;
-    return tc_attr<kGrad, true, kShortH>();
+    if ((e = tc_attr<kGrad, true, kShortH>())) return e;
+    return pair_setup();
 }
-
-namespace {
-
-// One kernel launch over the images of `a` whose tiles are h rows tall (all of them if `all`).
-cudaError_t tc_launch_height(const LaunchArgs &a, int mode, bool tf32, int h, bool all, int slots, int *d_status,
-                             cudaStream_t s)
-{
-    const LaunchArgs *p = &a;
-    LaunchArgs b;
-    if (!all) {
-        b = a;
-        b.nimg = 0;
-        b.tile_prefix[0] = 0;
-        for (int i = 0; i < a.nimg; ++i) {
-            if (a.img[i].tile_h != h) continue;
-            b.img[b.nimg] = a.img[i];
-            b.tile_prefix[b.nimg + 1] = b.tile_prefix[b.nimg] + (a.tile_prefix[i + 1] - a.tile_prefix[i]);
-            b.nimg++;
-        }
-        p = &b;
-    }
-    const int tiles = p->tile_prefix[p->nimg];
-    if (tiles <= 0) return cudaSuccess;
-    const int grid = std::min(tiles, slots);
-    if (tf32) return mode == kStep ? tc_launch_one<kStep, true, kShortH>(*p, grid, d_status, s)
-                                   : tc_launch_one<kGrad, true, kShortH>(*p, grid, d_status, s);
-    if (h == kTallH) return mode == kStep ? tc_launch_one<kStep, false, kTallH>(*p, grid, d_status, s)
-                                          : tc_launch_one<kGrad, false, kTallH>(*p, grid, d_status, s);
-    return mode == kStep ? tc_launch_one<kStep, false, kShortH>(*p, grid, d_status, s)
-                         : tc_launch_one<kGrad, false, kShortH>(*p, grid, d_status, s);
-}
-
-}  // namespace
 
 cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s)
 {
@@ -1053,13 +739,28 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int slots = 2 * sms;  // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
-    int ntall = 0;
-    for (int i = 0; i < a.nimg; ++i) ntall += a.img[i].tile_h == kTallH;
-    if (ntall == 0 || ntall == a.nimg)
-        return tc_launch_height(a, mode, tf32, ntall ? kTallH : kShortH, true, slots, d_status, s);
-    if ((e = tc_launch_height(a, mode, tf32, kTallH, false, slots, d_status, s)) != cudaSuccess) return e;
-    return tc_launch_height(a, mode, tf32, kShortH, false, slots, d_status, s);
+    // images tiled 58 x 58 run in the pixel-pair kernel (foe_pair.cu), the others (26 x 26 tiles, and every TF32
+    // image) here; a launch holding both kinds runs as one launch of each kernel
+    int npair = 0;
+    for (int i = 0; i < a.nimg; ++i) npair += a.img[i].tile_h == pair_tile();
+    if (npair > 0 && (e = pair_launch(a, mode, npair == a.nimg, sms, d_status, s)) != cudaSuccess) return e;
+    if (npair == a.nimg) return cudaSuccess;
+    LaunchArgs b = a;
+    b.nimg = 0;
+    b.tile_prefix[0] = 0;
+    for (int i = 0; i < a.nimg; ++i) {
+        if (a.img[i].tile_h == pair_tile()) continue;
+        b.img[b.nimg] = a.img[i];
+        b.tile_prefix[b.nimg + 1] = b.tile_prefix[b.nimg] + (a.tile_prefix[i + 1] - a.tile_prefix[i]);
+        b.nimg++;
+    }
+    const int tiles = b.tile_prefix[b.nimg];
+    // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
+    const int grid = std::min(tiles, 2 * sms);
+    if (tf32) return mode == kStep ? tc_launch_one<kStep, true, kShortH>(b, grid, d_status, s)
+                                   : tc_launch_one<kGrad, true, kShortH>(b, grid, d_status, s);
+    return mode == kStep ? tc_launch_one<kStep, false, kShortH>(b, grid, d_status, s)
+                         : tc_launch_one<kGrad, false, kShortH>(b, grid, d_status, s);
 }
 
 }  // namespace foe

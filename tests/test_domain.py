@@ -127,6 +127,9 @@ def _dying_worker(rank, world, port, q):
         q.put((rank, "finished", time.time() - t0))
     except Exception as e:  # the exchange with the lost neighbour fails instead of waiting forever
         q.put((rank, type(e).__name__, time.time() - t0))
+    # os._exit skips the queue's feeder thread: flush the message before leaving
+    q.close()
+    q.join_thread()
     os._exit(0)
 
 
