@@ -80,6 +80,11 @@ def lib() -> C.CDLL:
             L.orc_ipiano.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_int, _dp]
             L.orc_denoise.restype = C.c_int
             L.orc_denoise.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, _dp]
+            L.orc_ipiano_tol.restype = C.c_int
+            L.orc_ipiano_tol.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_int, C.c_double, C.c_int]
+            L.orc_denoise_tol.restype = C.c_int
+            L.orc_denoise_tol.argtypes = [C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                          C.c_int, _dp, C.POINTER(C.c_int)]
             L.orc_bin3.argtypes = [C.c_int, C.c_int, _dp, _dp]
             L.orc_upscale3.argtypes = [C.c_int, C.c_int, _dp, C.c_int, C.c_int, _dp]
             L.orc_denoise_binned.restype = C.c_int
@@ -327,6 +332,24 @@ class Problem:
         x = np.empty_like(y)
         used = lib().orc_denoise(C.byref(self.p), _p(y), float(peak), float(zero_c), int(iters), _p(x))
         return x, used
+
+    def ipiano_tol(self, d, u0, u_prev0, iters, tol, check_every):
+        """At most iters steps, stopping after step n (a multiple of check_every) once ||u^n - u^{n-1}|| <=
+        tol ||u^n||: (u, u_prev, steps taken)."""
+        d = _d(d)
+        u = _d(u0).copy()
+        up = _d(u_prev0).copy()
+        n = lib().orc_ipiano_tol(C.byref(self.p), _p(d), _p(u), _p(up), int(iters), float(tol), int(check_every))
+        return u, up, n
+
+    def denoise_tol(self, y, peak, iters, tol, check_every, zero_c=0.0):
+        """denoise with the stopping rule of ipiano_tol: (x, model used, steps taken)."""
+        y = _d(y)
+        x = np.empty_like(y)
+        done = C.c_int(0)
+        used = lib().orc_denoise_tol(C.byref(self.p), _p(y), float(peak), float(zero_c), int(iters), float(tol),
+                                     int(check_every), _p(x), C.byref(done))
+        return x, used, done.value
 
     def denoise_binned(self, y, peak, iters, zero_c=0.0):
         """FoEPNRbin: bin3, denoise the binned image at 9 * peak, upscale3 (the problem's H, W are the full sizes)."""

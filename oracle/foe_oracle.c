@@ -363,13 +363,52 @@ int orc_ipiano(const orc_params *p, const double *d, double *u, double *u_prev, 
     return 0;
 }
 
+/* Stopping rule (the paper fixes none; it reports the iteration counts of its runs, Sec. 5.1): after step n, for n
+ * a multiple of check_every, the solve stops at u^n once ||u^n - u^{n-1}||_2 <= tol ||u^n||_2 (sums in FP64).  Runs
+ * at most iters steps like orc_ipiano and returns the number of steps taken (tol <= 0: never stops early). */
+int orc_ipiano_tol(const orc_params *p, const double *d, double *u, double *u_prev, int iters, double tol,
+                   int check_every)
+{
+    const long N = (long)p->H * p->W;
+    double *un = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!un) return -1;
+    int n = 0;
+    while (n < iters) {
+        orc_ipiano_step(p, d, u, u_prev, un);
+        memcpy(u_prev, u, sizeof(double) * (size_t)N);
+        memcpy(u, un, sizeof(double) * (size_t)N);
+        ++n;
+        if (tol > 0.0 && check_every > 0 && n % check_every == 0) {
+            double dd = 0.0, uu = 0.0;
+            for (long i = 0; i < N; ++i) {
+                const double e = u[i] - u_prev[i];
+                dd += e * e;
+                uu += u[i] * u[i];
+            }
+            if (sqrt(dd) <= tol * sqrt(uu)) break;
+        }
+    }
+    free(un);
+    return n;
+}
+
 /* Whole denoiser for one image: data -> iPiano -> output.
  *   model 0 (direct, Eq. straightforward): d = y with zeros replaced by zero_c (Sec. 3.1.1),
  *           x = u^T;
  *   model 1/2 (Eq. overallModel / lowcase): d = Anscombe(y), x = I_C(max(u^T, sqrt(3/2)));
  *   model 3 (Eq. FOEscheme): 1 if peak >= 5 else 2.
  * Initial iterates u^0 = u^{-1} = d. */
+int orc_denoise_tol(const orc_params *p_in, const double *y, double peak, double zero_c, int iters, double tol,
+                    int check_every, double *x, int *iters_done);
+
 int orc_denoise(const orc_params *p_in, const double *y, double peak, double zero_c, int iters, double *x)
+{
+    return orc_denoise_tol(p_in, y, peak, zero_c, iters, 0.0, 0, x, NULL);
+}
+
+/* The same with the stopping rule of orc_ipiano_tol; *iters_done (nullable) receives the steps taken. */
+int orc_denoise_tol(const orc_params *p_in, const double *y, double peak, double zero_c, int iters, double tol,
+                    int check_every, double *x, int *iters_done)
 {
     orc_params p = *p_in;
     if (p.model == 3) p.model = (peak >= 5.0) ? 1 : 2;
@@ -385,7 +424,8 @@ int orc_denoise(const orc_params *p_in, const double *y, double peak, double zer
     }
     memcpy(u, d, sizeof(double) * (size_t)N);
     memcpy(up, d, sizeof(double) * (size_t)N);
-    orc_ipiano(&p, d, u, up, iters, NULL);
+    const int done = orc_ipiano_tol(&p, d, u, up, iters, tol, check_every);
+    if (iters_done) *iters_done = done;
     if (p.model == 0) memcpy(x, u, sizeof(double) * (size_t)N);
     else orc_inverse(N, u, x);
     free(d);

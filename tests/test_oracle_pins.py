@@ -327,6 +327,89 @@ def test_ipiano_converges_to_stationary_point_8x8(bank):
     assert np.abs(g).max() < 1e-5
 
 
+@pytest.mark.parametrize("model", [O.MODEL_ANS_L2, O.MODEL_ANS_IDIV])
+def test_ipiano_stationary_point_at_lambda_not_one(bank, model):
+    # lambda = 2.5: the limit solves grad R(u) + lambda grad D(u) = 0 with grad D written from the data terms of
+    # Eq. subproblemGL2 (u - d) and Eq. subproblemGIdiv (1 - d / u), and it is a local minimum of E = R + lambda D.
+    # A lambda dropped from the step's prox, from data_grad or from data_energy fails one of the three checks.
+    k, a = bank
+    lam, gamma = 2.5, 0.8
+    tau = _tau(k, a, O.BC_SYMMETRIC, gamma)
+    y = synth.poisson_observation(synth.clean_image(8, 8, 15), 4.0, 16)
+    d = O.anscombe(y)
+    pr = O.Problem(k, a, 8, 8, model=model, lam=lam, tau=tau, gamma=gamma, nthreads=1)
+    u, _ = pr.ipiano(d, d, d, 20000)
+    gd = (u - d) if model == O.MODEL_ANS_L2 else (1.0 - d / u)
+    gr = O.prior_grad(k, a, u, nthreads=1)
+    assert np.abs(gr + lam * gd).max() < 1e-6 * (1 + np.abs(gr).max())
+    assert np.abs(gr + gd).max() > 1e-2            # the lambda = 1 condition does not hold there
+    _, g = pr.energy_grad(u, d)
+    assert np.abs(g).max() < 1e-5
+    e0 = pr.energy(u, d)
+    rng = np.random.default_rng(5)
+    for _ in range(8):
+        v = rng.standard_normal(u.shape)
+        assert pr.energy(u + 1e-3 * v, d) > e0
+    # the energy's data part scales with lambda: E_lam(u) - E_1(u) = (lam - 1) D(u), D taken at lambda = 1
+    pr1 = O.Problem(k, a, 8, 8, model=model, lam=1.0, tau=tau, gamma=gamma, nthreads=1)
+    dat = 0.5 * float(((u - d) ** 2).sum()) if model == O.MODEL_ANS_L2 else float((u - d * np.log(u)).sum())
+    assert e0 - pr1.energy(u, d) == pytest.approx((lam - 1) * dat, rel=1e-10)
+
+
+# ----------------------------------------------------------------- stopping rule (reading of Sec. 5.1)
+
+
+def _data_only_stop(e0, gamma, tl, dn2, dv, vn2, tol, every, iters):
+    # With no prior (alpha = 0) and the quadratic data term, u^0 = u^{-1} = d + e0 v stays on the line d + e v:
+    # the prox of Eq. subproblemGL2 maps the inertial point d + (e_n + gamma (e_n - e_{n-1})) v to
+    # d + (e_n + gamma (e_n - e_{n-1})) / (1 + tau lambda) v.  Then |u^n - u^{n-1}| = |e_n - e_{n-1}| |v| and
+    # |u^n|^2 = |d|^2 + 2 e_n <d, v> + e_n^2 |v|^2, so the stopping step follows from the scalar recurrence.
+    e_prev, e = e0, e0
+    for n in range(1, iters + 1):
+        e_prev, e = e, (e + gamma * (e - e_prev)) / (1 + tl)
+        if n % every == 0 and abs(e - e_prev) * math.sqrt(vn2) <= tol * math.sqrt(dn2 + 2 * e * dv + e * e * vn2):
+            return n, e
+    return iters, e
+
+
+@pytest.mark.parametrize("tol,every", [(1e-3, 5), (3e-5, 1), (1e-6, 7), (0.2, 3)])
+def test_stopping_rule_data_only_closed_form(bank, tol, every):
+    k, a = bank
+    H = W = 10
+    lam, tau, gamma = 3.0, 0.05, 0.8
+    rng = np.random.default_rng(21)
+    d = rng.uniform(1.0, 6.0, (H, W))
+    v = rng.standard_normal((H, W))
+    pr = O.Problem(k, np.zeros_like(a), H, W, model=O.MODEL_ANS_L2, lam=lam, tau=tau, gamma=gamma, nthreads=1)
+    u0 = d + 1.0 * v
+    u, up, n = pr.ipiano_tol(d, u0, u0, 400, tol, every)
+    n_ref, e_ref = _data_only_stop(1.0, gamma, tau * lam, float((d * d).sum()), float((d * v).sum()),
+                                   float((v * v).sum()), tol, every, 400)
+    assert n == n_ref and 0 < n < 400 and n % every == 0
+    np.testing.assert_allclose(u, d + e_ref * v, rtol=0, atol=1e-12)
+
+
+def test_stopping_rule_special_cases(bank):
+    k, a = bank
+    y = synth.poisson_observation(synth.clean_image(12, 12, 31), 4.0, 32)
+    d = O.anscombe(y)
+    pr = O.Problem(k, a, 12, 12, model=O.MODEL_ANS_L2, lam=1.0, tau=1e-3, gamma=0.8, nthreads=1)
+    u_full, up_full = pr.ipiano(d, d, d, 30)
+    # tol = 0 never stops early, and a check interval beyond iters never checks: both equal the fixed-budget solve
+    for tol, every in [(0.0, 1), (10.0, 31)]:
+        u, up, n = pr.ipiano_tol(d, d, d, 30, tol, every)
+        assert n == 30 and np.array_equal(u, u_full) and np.array_equal(up, up_full)
+    # |u^n - u^{n-1}| <= |u^n| + |u^{n-1}|, so a tolerance above 1 + |u^{n-1}| / |u^n| stops at the first check
+    u, _, n = pr.ipiano_tol(d, d, d, 30, 10.0, 4)
+    u4, _ = pr.ipiano(d, d, d, 4)
+    assert n == 4 and np.array_equal(u, u4)
+    # the whole denoiser with the rule equals the fixed-budget denoiser run for the steps it took
+    x, used, n = pr.denoise_tol(y, 4.0, 300, 2e-4, 10)
+    assert 0 < n < 300 and n % 10 == 0
+    xr, _ = pr.denoise(y, 4.0, n)
+    assert np.array_equal(x, xr)
+
+
 def test_denoise_model_selection_and_pipeline(bank):
     # Eq. FOEscheme: peak >= 5 -> quadratic data term, peak < 5 -> I-divergence (Anscombe domain).
     k, a = bank
