@@ -82,7 +82,12 @@ typedef struct {
     float lambda;         /* data-term weight, > 0 */
     float gamma;          /* inertia, 0 <= gamma < 1 */
     float tau;            /* step size; 0 = the context's default for (bc, gamma) */
-    float tol;            /* reserved (0): iterations always run to `iters` */
+    float tol;            /* stopping rule, >= 0 (0: every solve runs its whole iteration budget).  The paper
+                             runs iPiano to convergence and reports the iteration counts (Sec. 5.1) without
+                             fixing a rule; the rule here: after step n, n a multiple of tol_every, an image
+                             stops at u^n once ||u^n - u^{n-1}||_2 <= tol ||u^n||_2, both norms summed in
+                             FP64 on the device in a fixed order.  The output is then the map of u^n; the
+                             budget (`iters`, or the desc's) caps n.  foe_iters_done returns the counts. */
     int iters;            /* >= 0 */
     foe_step_mode step;   /* FIXED: constant tau.  BACKTRACK (foe_denoise with FOE_PREC_FP32 only; the other
                              entry points return FOE_EUNSUPPORTED): Lipschitz backtracking on the prior, see
@@ -95,6 +100,8 @@ typedef struct {
                              non-default stream (on the legacy default stream the launches are issued
                              directly).  The instantiated graph is cached in the context and updated in
                              place when the next batch has the same launch structure. */
+    int tol_every;        /* check interval of the stopping rule, >= 1 when tol > 0.  A check reads the
+                             iterate and its last change once (8 bytes per pixel, 12 on the FP32 path). */
 } foe_solve_opts;
 
 typedef struct {
@@ -116,8 +123,9 @@ typedef struct {
     int iters;            /* per-image iteration budget, >= 0 */
 } foe_image_desc;
 
-/* Fills *opts with the defaults: AUTO model, lambda 1, gamma 0.8, tau 0 (auto), 300 iterations,
- * fixed steps, symmetric padding, BF16 convolutions, zero_c 0, no graph capture. */
+/* Fills *opts with the defaults: AUTO model, lambda 1, gamma 0.8, tau 0 (auto), no stopping rule (tol 0,
+ * tol_every 10), 300 iterations, fixed steps, symmetric padding, BF16 convolutions, zero_c 0, no graph
+ * capture. */
 FOE_API foe_status foe_default_opts(foe_solve_opts *opts);
 
 /* Creates a context for one prior: validates it, copies the filters to the device and precomputes
@@ -158,7 +166,11 @@ FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted
  * otherwise L doubles and the step is retried from the same u; after each accepted step L is divided by 1.5.
  * L starts at the bound of foe_step_size (or at the L implied by opts.tau when it is > 0).  The host reads
  * three scalars per trial (one synchronisation each), so this mode is for accuracy, not throughput.
- * foe_step_log returns the trials of the last such solve. */
+ * foe_step_log returns the trials of the last such solve.
+ * With opts.tol > 0 (fixed steps) the host reads the image's stopping word one check interval behind the
+ * device (an event on the stream; the next interval is queued meanwhile), issues no launch past the interval
+ * after the stop, and step launches after the stop leave the image unchanged.  On a stream under capture the
+ * whole budget is queued and the launches past the stop do no work. */
 FOE_API foe_status foe_denoise(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                        const foe_solve_opts *opts, void *stream, foe_report *rep);
 
@@ -190,7 +202,8 @@ FOE_API foe_status foe_denoise_binned(foe_ctx *ctx, const float *y, float *x, in
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress), with
  *     that device current; make that first call before any stream capture begins.
  *   - No report and no profiling: nothing is synchronised.  The context (created earlier, when
- *     allocation was possible) supplies the filters.
+ *     allocation was possible) supplies the filters.  With opts.tol > 0 the whole budget is queued and
+ *     the launches past the stop do no work; foe_iters_done gives the count afterwards.
  *   - A device-side wait of the tensor-core kernel that expired earlier in this context (FOE_ETIMEOUT,
  *     sticky until read) makes every later tensor-core step launch of the context return at once.  This
  *     call cannot read that status without synchronising, so on the BF16 / TF32 paths its output map then
@@ -202,9 +215,18 @@ FOE_API foe_status foe_denoise_static(foe_ctx *ctx, const float *y, float *x, in
 
 /* Denoises n independent images of mixed sizes and iteration budgets in one stream-ordered pass:
  * every iteration advances all images whose budget is not yet spent, in one launch over the tiles
- * of all of them.  opts->iters is ignored (each desc carries its own). */
+ * of all of them.  opts->iters is ignored (each desc carries its own).  With opts->tol > 0 every image has
+ * its own stopping word: the whole budget is queued (nothing is synchronised), and the step launches skip
+ * the tiles of images that have stopped, so a launch in which every image has stopped does almost no work. */
 FOE_API foe_status foe_denoise_batch(foe_ctx *ctx, const foe_image_desc *descs, int n, const foe_solve_opts *opts,
                              void *stream);
+
+/* Iterations taken by the images of the context's last foe_denoise, foe_denoise_static or foe_denoise_batch
+ * solve (fixed steps): out[i] for image i in the order of the call (n = 1 for the single-image calls), the
+ * step of the stopping rule's first success, or the image's budget when it never held or opts.tol was 0.
+ * Synchronises the stream the solve ran on (pass it), reads n words from the device.
+ *   out  host, n ints; n must equal the last solve's image count (FOE_EINVAL otherwise, or before any solve) */
+FOE_API foe_status foe_iters_done(foe_ctx *ctx, int *out, int n, void *stream);
 
 /* Energy and gradient of E = F + D at u (Eq. FOEmodel + the model's data term; gradient Eq. FoEF plus
  * grad D).  model must be DIRECT, ANS_L2 or ANS_IDIV; data is y (DIRECT) or v (Anscombe models).
@@ -222,7 +244,8 @@ FOE_API foe_status foe_energy_grad(foe_ctx *ctx, const float *u, const float *da
  * backward kernel (Hessian-vector products of the prior, Sec. 2.5.2).  Iterates are checkpointed every
  * ckpt_every steps (0: about sqrt(T)) and recomputed segment by segment in the reverse sweep.
  *   clean, noisy  device, B images of H x W, row pitch ld, image stride H * ld floats (g_s and y_s)
- *   opts          model must be FOE_MODEL_ANS_L2, prec FOE_PREC_FP32; lambda, gamma, tau (0: default), bc
+ *   opts          model must be FOE_MODEL_ANS_L2, prec FOE_PREC_FP32; lambda, gamma, tau (0: default), bc;
+ *                 tol must be 0 (FOE_EUNSUPPORTED otherwise: the T steps are the differentiated function)
  *   loss_host     host, nullable: L (synchronises the stream)
  *   dfilters      device, [nf][49], dL/dk_i(a, b) in the filters' convolution orientation
  *   dlogalpha     device, [nf], dL/da_i
@@ -284,7 +307,8 @@ typedef struct {
     int max_active;           /* requests iterated together, 1..64 */
     int iters_per_tick;       /* iterations each admitted request advances per tick, >= 1 */
     int use_graphs;           /* 1: each tick's step launches are captured and replayed as a CUDA graph */
-    foe_solve_opts opts;      /* model, lambda, gamma, tau, bc, prec, zero_c for every request; iters ignored */
+    foe_solve_opts opts;      /* model, lambda, gamma, tau, bc, prec, zero_c for every request; iters ignored;
+                                 tol must be 0 (FOE_EUNSUPPORTED otherwise) */
 } foe_server_config;
 
 typedef struct {

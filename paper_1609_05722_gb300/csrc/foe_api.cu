@@ -11,6 +11,8 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
     std::vector<Slot> slots(n);
     std::vector<int> models(n);
     float *base = (float *)c->ws;
+    const bool tol_on = o->tol > 0.0f;
+    if (tol_on) FOE_CUDA(c, cudaMemsetAsync(c->d_stop, 0, sizeof(int) * n, s));
     args_begin(c, o->bc);
     for (int j = 0; j < n; ++j) {
         const foe_image_desc &d = descs[order[j]];
@@ -32,6 +34,7 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
         e.ld = d.ld;
         e.model = models[j];
         e.sc = step_consts(tau, o->gamma, o->lambda);
+        e.stop = tol_on ? c->d_stop + j : nullptr;
         args_add(c, o->prec, e);
     }
     const int nall = c->args.nimg;
@@ -46,7 +49,8 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
         }
         c->args.nimg = active;
         c->args.parity = it & 1;
-        if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) {
+        if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK ||
+            (tol_on && (it + 1) % o->tol_every == 0 && (st = tol_check(c, active, it + 1, o->tol, s)) != FOE_OK)) {
             c->args.nimg = nall;
             return st;
         }
@@ -55,8 +59,9 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
     if (profile && (st = prof_end(c, s, ev, max_iters, pix)) != FOE_OK) return st;
     for (int j = 0; j < n; ++j) {
         const foe_image_desc &d = descs[order[j]];
-        const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0;
-        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, slots[j].ul), d.H, d.W, d.ld, d.ld, models[j], d.x, nullptr, s));
+        const float *uf = (d.iters & 1) ? slots[j].uh1 : slots[j].uh0, *ua = (d.iters & 1) ? slots[j].uh0 : slots[j].uh1;
+        FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, slots[j].ul), d.H, d.W, d.ld, d.ld, models[j], d.x, nullptr, s,
+                                       nullptr, ua, d.iters, tol_on ? c->d_stop + j : nullptr));
     }
     return FOE_OK;
 }
@@ -95,6 +100,7 @@ foe_status foe_default_opts(foe_solve_opts *o)
     o->prec = FOE_PREC_BF16;
     o->zero_c = 0.0f;
     o->use_graph = 0;
+    o->tol_every = 10;
     return FOE_OK;
 }
 
@@ -141,6 +147,15 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         (e = cudaMemcpy(c->d_alpha, c->alpha, sizeof(c->alpha), cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(c->d_status, 0, sizeof(int))) || (e = foe::f32_setup()) || (e = foe::tc_setup()) || (e = foe::bwd_setup()))
         return fail(e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA);
+    if ((e = cudaMalloc(&c->d_stop, sizeof(int) * foe::kMaxBatch)) ||
+        (e = cudaMalloc(&c->d_tol_part, sizeof(double) * 2 * foe::kTolBlocks * foe::kMaxBatch)) ||
+        (e = cudaMalloc(&c->d_tol_count, sizeof(unsigned) * foe::kMaxBatch)) ||
+        (e = cudaMemset(c->d_stop, 0, sizeof(int) * foe::kMaxBatch)) ||
+        (e = cudaMemset(c->d_tol_count, 0, sizeof(unsigned) * foe::kMaxBatch)) ||
+        (e = cudaHostAlloc(&c->h_stop, 2 * sizeof(int), cudaHostAllocDefault)) ||
+        (e = cudaEventCreateWithFlags(&c->tol_ev[0], cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->tol_ev[1], cudaEventDisableTiming)))
+        return fail(e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA);
     if (ensure_partials(c, 1024) != FOE_OK) return fail(FOE_ENOMEM);
     *out = c;
     return FOE_OK;
@@ -161,6 +176,12 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_partials);
     cudaFree(c->ws);
     cudaFree(c->d_bin);
+    cudaFree(c->d_stop);
+    cudaFree(c->d_tol_part);
+    cudaFree(c->d_tol_count);
+    if (c->h_stop) cudaFreeHost(c->h_stop);
+    for (cudaEvent_t e : c->tol_ev)
+        if (e) cudaEventDestroy(e);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     delete c;
 }
@@ -233,6 +254,9 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
     }
     c->bt_tau.clear();
     c->bt_accepted.clear();
+    const bool tol_on = o->tol > 0.0f;
+    if (tol_on) FOE_CUDA(c, cudaMemsetAsync(c->d_stop, 0, sizeof(int), s));
+    int done = o->iters;
     double h[3], Fn = 0.0;
     if ((st = prior_energy(sl.uh0, outs + 2)) != FOE_OK) return st;
     FOE_CUDA(c, cudaMemcpyAsync(&Fn, outs + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -277,7 +301,26 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         }
         std::swap(cur, nxt);
         L /= 1.5;
+        if (tol_on && (n + 1) % o->tol_every == 0) {
+            // the host waits on every trial here anyway: check u^{n+1} and read the word at once
+            foe::TolArgs t;
+            t.nimg = 1;
+            t.n = n + 1;
+            t.tol = (double)o->tol;
+            t.partials = c->d_tol_part;
+            t.count = c->d_tol_count;
+            t.img[0] = foe::TolImg{cur, sl.ul, sl.delta, H, W, ld, c->d_stop};
+            FOE_CUDA(c, foe::launch_tol_check(t, s));
+            FOE_CUDA(c, cudaMemcpyAsync(c->h_stop, c->d_stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FOE_CUDA(c, cudaStreamSynchronize(s));
+            if (c->h_stop[0] != 0) {
+                done = n + 1;
+                break;
+            }
+        }
     }
+    const int word = tol_on ? 0 : -1;
+    note_solve(c, 1, &o->iters, &word);
     if (rep) FOE_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), s));
     FOE_CUDA(c, foe::launch_output(cur, sl.ul, H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s));
     if (rep) {
@@ -286,7 +329,7 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         FOE_CUDA(c, cudaMemcpyAsync(&nonfinite, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaStreamSynchronize(s));
         rep->nonfinite = nonfinite;
-        rep->iters_done = o->iters;
+        rep->iters_done = done;
         rep->model_used = model;
         rep->tau_used = tau;
         rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
@@ -334,24 +377,50 @@ foe_status foe_denoise(foe_ctx *c, const float *y, float *x, int H, int W, int l
     d.ld = ld;
     d.model = model;
     d.sc = step_consts(tau, o->gamma, o->lambda);
+    const bool tol_on = o->tol > 0.0f;
+    if (tol_on) {
+        FOE_CUDA(c, cudaMemsetAsync(c->d_stop, 0, sizeof(int), s));
+        d.stop = c->d_stop;
+    }
     args_add(c, o->prec, d);
+    // the host follows the stopping word one check interval behind the device, unless the stream is captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (tol_on) FOE_CUDA(c, cudaStreamIsCapturing(s, &cap));
+    const bool follow = tol_on && cap == cudaStreamCaptureStatusNone;
     cudaEvent_t ev[2];
     if ((st = prof_begin(c, s, ev)) != FOE_OK) return st;
+    int launched = 0, checks = 0;
     for (int n = 0; n < o->iters; ++n) {
         c->args.parity = n & 1;
         if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
+        ++launched;
+        if (!tol_on || (n + 1) % o->tol_every != 0) continue;
+        if ((st = tol_check(c, 1, n + 1, o->tol, s)) != FOE_OK) return st;
+        if (!follow) continue;
+        const int slot = checks++ & 1;
+        FOE_CUDA(c, cudaMemcpyAsync(c->h_stop + slot, c->d_stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FOE_CUDA(c, cudaEventRecord(c->tol_ev[slot], s));
+        if (checks > 1) {
+            // the previous check's word (this interval's launches keep the device busy meanwhile)
+            FOE_CUDA(c, cudaEventSynchronize(c->tol_ev[slot ^ 1]));
+            if (c->h_stop[slot ^ 1] != 0) break;
+        }
     }
-    if ((st = prof_end(c, s, ev, o->iters, (double)H * W * o->iters)) != FOE_OK) return st;
-    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
+    if ((st = prof_end(c, s, ev, launched, (double)H * W * launched)) != FOE_OK) return st;
+    const int word = tol_on ? 0 : -1;
+    note_solve(c, 1, &o->iters, &word);
+    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0, *ua = (o->iters & 1) ? sl.uh0 : sl.uh1;
     if (rep) FOE_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), s));
-    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s,
+                                   nullptr, ua, o->iters, tol_on ? c->d_stop : nullptr));
     if (rep) {
-        int dev_status = 0, nonfinite = 0;
+        int dev_status = 0, nonfinite = 0, stop = 0;
         FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaMemcpyAsync(&nonfinite, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (tol_on) FOE_CUDA(c, cudaMemcpyAsync(&stop, c->d_stop, sizeof(int), cudaMemcpyDeviceToHost, s));
         FOE_CUDA(c, cudaStreamSynchronize(s));
         rep->nonfinite = nonfinite;
-        rep->iters_done = o->iters;
+        rep->iters_done = stop ? stop : o->iters;
         rep->model_used = model;
         rep->tau_used = tau;
         rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
@@ -448,6 +517,15 @@ foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, con
     // images with larger budgets first: the active set of every iteration is a prefix
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return descs[a].iters > descs[b].iters; });
     if ((st = ensure_ws(c, total * sizeof(float))) != FOE_OK) return st;
+    {
+        // image order[j] of the call holds stopping word j
+        std::vector<int> budget(n), word(n, -1);
+        for (int j = 0; j < n; ++j) {
+            budget[order[j]] = descs[order[j]].iters;
+            if (o->tol > 0.0f) word[order[j]] = j;
+        }
+        note_solve(c, n, budget.data(), word.data());
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     FOE_CUDA(c, cudaStreamIsCapturing(s, &cap));
@@ -487,6 +565,28 @@ foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, con
     double pix = 0.0;
     for (int j = 0; j < n; ++j) pix += (double)descs[j].H * descs[j].W * descs[j].iters;
     return prof_end(c, s, ev, max_iters, pix);
+}
+
+foe_status foe_iters_done(foe_ctx *c, int *out, int n, void *stream)
+{
+    if (!c) return FOE_EINVAL;
+    if (!out || n < 1 || (size_t)n != c->last_budget.size()) {
+        set_err(c, "foe_iters_done: n must equal the image count of the last solve (%zu)", c->last_budget.size());
+        return FOE_EINVAL;
+    }
+    int words = 0;
+    for (int w : c->last_word) words = std::max(words, w + 1);
+    std::vector<int> stop(std::max(words, 1), 0);
+    if (words > 0) {
+        cudaStream_t s = (cudaStream_t)stream;
+        FOE_CUDA(c, cudaMemcpyAsync(stop.data(), c->d_stop, sizeof(int) * words, cudaMemcpyDeviceToHost, s));
+        FOE_CUDA(c, cudaStreamSynchronize(s));
+    }
+    for (int i = 0; i < n; ++i) {
+        const int w = c->last_word[i];
+        out[i] = (w >= 0 && stop[w] != 0) ? stop[w] : c->last_budget[i];
+    }
+    return FOE_OK;
 }
 
 foe_status foe_energy_grad(foe_ctx *c, const float *u, const float *data, int H, int W, int ld, foe_model model,
@@ -697,16 +797,25 @@ extern "C" foe_status foe_denoise_static(foe_ctx *c, const float *y, float *x, i
     d.ld = ld;
     d.model = model;
     d.sc = step_consts(tau, o->gamma, o->lambda);
+    const bool tol_on = o->tol > 0.0f;
+    if (tol_on) {
+        FOE_CUDA(c, cudaMemsetAsync(c->d_stop, 0, sizeof(int), s));
+        d.stop = c->d_stop;
+    }
     args_add(c, o->prec, d);
     for (int n = 0; n < o->iters; ++n) {
         c->args.parity = n & 1;
         if ((st = launch(c, o->prec, foe::kStep, s)) != FOE_OK) return st;
+        if (tol_on && (n + 1) % o->tol_every == 0 && (st = tol_check(c, 1, n + 1, o->tol, s)) != FOE_OK) return st;
     }
-    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0;
+    const int word = tol_on ? 0 : -1;
+    note_solve(c, 1, &o->iters, &word);
+    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0, *ua = (o->iters & 1) ? sl.uh0 : sl.uh1;
     // no status is read back here (nothing is synchronised): on the tensor-core paths, whose step launches do
     // nothing while the context's device status is set, an expired device wait shows as a NaN output
     const int *guard = o->prec == FOE_PREC_FP32 ? nullptr : c->d_status;
-    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, nullptr, s, guard));
+    FOE_CUDA(c, foe::launch_output(uf, lo_plane(o->prec, sl.ul), H, W, ld, ld, model, x, nullptr, s, guard, ua, o->iters,
+                                   tol_on ? c->d_stop : nullptr));
     return FOE_OK;
 }
 

@@ -40,6 +40,8 @@ struct ImgDesc {
     int tile_h;                // tensor-core path: output rows of this image's tiles
     int model;
     StepConsts sc;
+    const int *stop;           // nullable: the image's stopping word; non-zero once its stopping rule has held (the
+                               // step count at that check), after which every step launch leaves the image as it is
 };
 
 struct LaunchArgs {
@@ -191,6 +193,10 @@ __device__ __forceinline__ double data_energy(float u, float d, int model, float
     if (dd == 0.0) return lambda * ud;
     return lambda * (ud - dd * log(ud));
 }
+
+// True when the image's stopping rule has held.  The word is written by the stopping check, a launch of its own
+// between two step launches, and read here after any griddepcontrol.wait (L2, not a possibly stale L1 line).
+__device__ __forceinline__ bool image_stopped(const ImgDesc &d) { return d.stop && __ldcg(d.stop) != 0; }
 
 // Image index of a flat tile index (binary search over the launch's tile prefix).
 __device__ __forceinline__ int tile_image(const LaunchArgs &a, int tile)

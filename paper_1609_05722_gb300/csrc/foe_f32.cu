@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
     const int tile = blockIdx.x;
     const int im = tile_image(A, tile);
     const ImgDesc &D = A.img[im];
+    if (image_stopped(D)) return;  // CTA-uniform
     const int lt = tile - A.tile_prefix[im];
     const int ty0 = (lt / D.tiles_x) * T, tx0 = (lt % D.tiles_x) * T;
     const int H = D.H, W = D.W, ld = D.ld;
@@ -266,13 +267,17 @@ __device__ __forceinline__ double inv_anscombe(double z)
 // status (nullable): the context's sticky device status; while it is set the solve's step launches did nothing,
 // so the output is NaN rather than a stale iterate (for callers that return without reading the status)
 __global__ void k_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x,
-                         int *nonfinite, const int *status)
+                         int *nonfinite, const int *status, const float *uh_alt, int budget, const int *stop)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (c >= W || r >= H) return;
     if (status && *(const volatile int *)status != 0) {
         x[(size_t)r * xld + c] = __int_as_float(0x7fc00000);
         return;
+    }
+    if (stop) {
+        const int n = __ldcg(stop);
+        if (n != 0 && ((n ^ budget) & 1)) uh = uh_alt;
     }
     const size_t i = (size_t)r * ld + c;
     const double u = (double)uh[i] + (ul ? (double)ul[i] : 0.0);
@@ -343,10 +348,10 @@ cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model
 }
 
 cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x, int *nonfinite,
-                          cudaStream_t s, const int *status)
+                          cudaStream_t s, const int *status, const float *uh_alt, int budget, const int *stop)
 {
     dim3 g((W + 127) / 128, H);
-    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x, nonfinite, status);
+    k_output<<<g, 128, 0, s>>>(uh, ul, H, W, ld, xld, model, x, nonfinite, status, uh_alt, budget, stop);
     return cudaGetLastError();
 }
 

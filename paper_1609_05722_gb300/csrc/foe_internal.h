@@ -39,6 +39,15 @@ struct foe_ctx {
     int *d_status = nullptr;
     int *d_nonfinite = nullptr;             // non-finite outputs of the last reporting solve
     int withhold_arrival = 0;               // foe_debug_withhold_arrival: applies to the next tensor-core launch
+    // stopping rule (opts.tol): one word per image of a solve, the check's FP64 partials and block counts, and two
+    // pinned words with events through which foe_denoise reads its word one check interval behind the device
+    int *d_stop = nullptr;                  // [kMaxBatch]
+    double *d_tol_part = nullptr;           // [kMaxBatch][kTolBlocks][2]
+    unsigned *d_tol_count = nullptr;        // [kMaxBatch], 0 between checks
+    int *h_stop = nullptr;                  // pinned [2]
+    cudaEvent_t tol_ev[2] = {nullptr, nullptr};
+    // the last fixed-step solve (foe_iters_done): per image of the call, its budget and its word (-1: none)
+    std::vector<int> last_budget, last_word;
     LaunchArgs args;
     // step-loop timing (foe_profile)
     bool prof = false;
@@ -239,6 +248,18 @@ inline foe_status check_opts(foe_ctx *c, const foe_solve_opts *o)
         return FOE_EINVAL;
     }
     if (!(o->zero_c >= 0.0f) || !std::isfinite(o->zero_c)) { set_err(c, "zero_c must be >= 0"); return FOE_EINVAL; }
+    if (!(o->tol >= 0.0f) || !std::isfinite(o->tol)) { set_err(c, "tol must be >= 0"); return FOE_EINVAL; }
+    if (o->tol > 0.0f && o->tol_every < 1) { set_err(c, "tol_every must be >= 1 when tol > 0"); return FOE_EINVAL; }
+    return FOE_OK;
+}
+
+// Entry points that run every iteration of their budget (training, serving) take no stopping rule.
+inline foe_status check_no_tol(foe_ctx *c, const foe_solve_opts *o, const char *entry)
+{
+    if (o && o->tol > 0.0f) {
+        set_err(c, "%s: opts.tol > 0 is not supported here (every iteration of the budget runs)", entry);
+        return FOE_EUNSUPPORTED;
+    }
     return FOE_OK;
 }
 
@@ -414,6 +435,42 @@ inline float *lo_plane(int prec, float *ul) { return prec == FOE_PREC_FP32 ? ul 
 struct Slot {
     float *uh0, *uh1, *ul, *delta, *d;
 };
+
+// Stopping check after step n: the iterate u^n (plane n & 1) and its change of the listed images.
+inline foe::TolImg tol_img(const ImgDesc &d, int n)
+{
+    foe::TolImg t;
+    t.u_hi = d.u_hi[n & 1];
+    t.u_lo = d.u_lo;
+    t.delta = d.delta;
+    t.H = d.H;
+    t.W = d.W;
+    t.ld = d.ld;
+    t.stop = const_cast<int *>(d.stop);
+    return t;
+}
+
+// Checks the images 0 .. nimg - 1 of the context's launch arguments that carry a stopping word.
+inline foe_status tol_check(foe_ctx *c, int nimg, int n, float tol, cudaStream_t s)
+{
+    foe::TolArgs t;
+    t.nimg = 0;
+    t.n = n;
+    t.tol = (double)tol;
+    t.partials = c->d_tol_part;
+    t.count = c->d_tol_count;
+    for (int j = 0; j < nimg; ++j)
+        if (c->args.img[j].stop) t.img[t.nimg++] = tol_img(c->args.img[j], n);
+    FOE_CUDA(c, foe::launch_tol_check(t, s));
+    return FOE_OK;
+}
+
+// Records the images of a fixed-step solve for foe_iters_done.
+inline void note_solve(foe_ctx *c, int n, const int *budget, const int *word)
+{
+    c->last_budget.assign(budget, budget + n);
+    c->last_word.assign(word, word + n);
+}
 
 inline Slot carve(float *base, size_t plane)
 {

@@ -41,9 +41,30 @@ cudaError_t launch_copy(const float *src, float *dst, long n, cudaStream_t s);
 cudaError_t launch_init(const float *y, int H, int W, int yld, int ld, int model, float zero_c, float *d, float *uh,
                         float *ul, float *delta, cudaStream_t s);
 // x = the output map of the iterate; *nonfinite (nullable) += the number of non-finite outputs; x = NaN while
-// *status (nullable: not checked) is non-zero
+// *status (nullable: not checked) is non-zero.  With a stopping word (stop non-null) the iterate is read from uh when
+// the step count, *stop if non-zero and `budget` otherwise, has the parity of `budget`, and from uh_alt when not.
 cudaError_t launch_output(const float *uh, const float *ul, int H, int W, int ld, int xld, int model, float *x, int *nonfinite,
-                          cudaStream_t s, const int *status = nullptr);
+                          cudaStream_t s, const int *status = nullptr, const float *uh_alt = nullptr, int budget = 0,
+                          const int *stop = nullptr);
+
+// Stopping check (foe_tol.cu) after step n of the images of a launch: for every image whose word is still 0, in
+// FP64 and a fixed summation order, dd = sum (u^n - u^{n-1})^2 (the delta plane) and uu = sum (u_hi + u_lo)^2; the
+// word becomes n when sqrt(dd) <= tol sqrt(uu).
+constexpr int kTolBlocks = 32;    // blocks per image (rows b, b + kTolBlocks, ...)
+struct TolImg {
+    const float *u_hi, *u_lo;     // u^n (u_lo nullable: 0)
+    const float *delta;           // u^n - u^{n-1}
+    int H, W, ld;
+    int *stop;
+};
+struct TolArgs {
+    int nimg, n;
+    double tol;
+    double *partials;             // [kMaxBatch][kTolBlocks][2]
+    unsigned *count;              // [kMaxBatch], 0 between checks
+    TolImg img[kMaxBatch];
+};
+cudaError_t launch_tol_check(const TolArgs &a, cudaStream_t s);
 cudaError_t launch_anscombe(const float *y, float *v, long n, cudaStream_t s);
 cudaError_t launch_inverse(const float *z, float *x, long n, cudaStream_t s);
 cudaError_t launch_reduce(const double *p, int n, double *out, cudaStream_t s);

@@ -109,6 +109,7 @@ struct PairSmem {
     float O[kORing][3][2][128];          // output-pass operands (u, delta, d of both pixels) of the next steps
     int tprefix[kMaxBatch + 1];
     int timg[kMaxBatch][3];              // tiles per row, H, W
+    int live[kMaxBatch];                 // 0 once the image's stopping rule has held (its tiles are skipped)
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void pair_axis(int t, int n, int L, int &o, int &s, i
     }
 }
 
-__device__ __forceinline__ Geo pair_geometry(const PairSmem &S, int nimg, int tile)
+__device__ __forceinline__ int pair_image(const PairSmem &S, int nimg, int tile)
 {
     int lo = 0, hi = nimg - 1;
     while (lo < hi) {
@@ -157,6 +158,19 @@ __device__ __forceinline__ Geo pair_geometry(const PairSmem &S, int nimg, int ti
         if (S.tprefix[mid] <= tile) lo = mid;
         else hi = mid - 1;
     }
+    return lo;
+}
+
+// The CTA's tiles are tile0, tile0 + gridDim.x, ... without those of stopped images: every role walks the same list.
+__device__ __forceinline__ int pair_next_live(const PairSmem &S, int nimg, int ntiles, int tile)
+{
+    while (tile < ntiles && !S.live[pair_image(S, nimg, tile)]) tile += gridDim.x;
+    return tile;
+}
+
+__device__ __forceinline__ Geo pair_geometry(const PairSmem &S, int nimg, int tile)
+{
+    const int lo = pair_image(S, nimg, tile);
     Geo g;
     g.im = lo;
     const int tiles_x = S.timg[lo][0];
@@ -512,11 +526,14 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         S.timg[tid][1] = A.img[tid].H;
         S.timg[tid][2] = A.img[tid].W;
     }
-    // from here on the previous step's results (the iterate, *status) are read
+    // from here on the previous step's results (the iterate, *status, the stopping words) are read
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0) S.abort_flag = *(volatile int *)status;
+    if (tid < A.nimg) S.live[tid] = !image_stopped(A.img[tid]);
     __syncthreads();
     if (S.abort_flag) return;  // an earlier launch gave up: do nothing (CTA-uniform)
+    const int tile0 = pair_next_live(S, A.nimg, ntiles, blockIdx.x);
+    if (tile0 >= ntiles) return;  // every tile of this CTA belongs to a stopped image (CTA-uniform)
     if (warp == FWDW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
                      "r"(kTmemCols)
@@ -533,6 +550,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
     const uint32_t tmem = S.tmem_base;
     volatile int *abort_flag = &S.abort_flag;
     const int stride = gridDim.x;
+    auto next = [&](int tile) { return pair_next_live(S, A.nimg, ntiles, tile); };
 
     if (warp < NEXP) {
         // ---------------- expert: R(g) -> Psi(g) ----------------
@@ -544,7 +562,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         uint32_t rph = 0, pph = 0;
         long long gm = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < ntiles; tile += stride) {
+        for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride)) {
             const Geo g = pair_geometry(S, A.nimg, tile);
             const bool interior = g.oy0 >= 3 && g.ox0 >= 3 && g.oy0 + PT + 3 <= g.H && g.ox0 + PT + 3 <= g.W;
             const int gx0 = g.ox0 - 3 + 2 * lane;
@@ -613,7 +631,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         uint32_t ph = 0;
         bool ok = true;
         int k = 0;
-        for (int tile = blockIdx.x; ok && tile < ntiles; tile += stride, ++k) {
+        for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride), ++k) {
             const Geo g = pair_geometry(S, A.nimg, tile);
             // the lanes at the warp's edges get no shuffled values from outside the region; their sums are used only
             // by the padding fold of a tile at the left or right image border, where the missing terms are zero
@@ -691,7 +709,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         uint32_t ph = 0;
         int k = 0;
         long long g = 0;
-        for (int tile = blockIdx.x; ok && tile < ntiles; tile += stride, ++k) {
+        for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride), ++k) {
             const int b = k & 1;
             if (!mbar_wait_warp(&S.bar[B_EREADY + b], (k >> 1) & 1, abort_flag, status)) break;
             fence_after();
@@ -722,7 +740,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         int ps = 0, zs = 0;
         uint32_t pph = 0, zph = 0;
         long long g = 0;
-        for (int tile = blockIdx.x; ok && tile < ntiles; tile += stride) {
+        for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride)) {
             for (int t = 0; t < PNMT; ++t, ++g) {
                 if (!mbar_wait_warp(&S.bar[B_PSI + ps], pph, abort_flag, status) ||
                     (g >= NZST && !mbar_wait_warp(&S.bar[B_ZFREE + zs], zph ^ 1u, abort_flag, status))) {
@@ -747,7 +765,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         // ---------------- output pass of each tile ----------------
         bool ok = true;
         int k = 0;
-        for (int tile = blockIdx.x; ok && tile < ntiles; tile += stride, ++k)
+        for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride), ++k)
             ok = output_tile<MODE>(A, S, tile, k, tid - 32 * OUTW0, abort_flag, status);
         cp_async_wait<0>();
     } else {
@@ -779,17 +797,18 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
             fence_async_smem();
             mbar_arrive(&S.bar[B_EREADY + b]);
             if (!prod_all(true)) return false;  // the region is consumed
-            if (tile + stride < ntiles) {
-                r_next = stage_region(A, S, pair_geometry(S, A.nimg, tile + stride), p);
+            const int tn = next(tile + stride);
+            if (tn < ntiles) {
+                r_next = stage_region(A, S, pair_geometry(S, A.nimg, tn), p);
                 pending = true;
             }
             return true;
         };
-        r_next = stage_region(A, S, pair_geometry(S, A.nimg, blockIdx.x), p);
+        r_next = stage_region(A, S, pair_geometry(S, A.nimg, tile0), p);
         pending = true;
-        ok = build(blockIdx.x, 0);
+        ok = build(tile0, 0);
         int k = 1;
-        for (int tile = blockIdx.x + stride; ok && tile < ntiles; tile += stride, ++k) ok = build(tile, k);
+        for (int tile = next(tile0 + stride); ok && tile < ntiles; tile = next(tile + stride), ++k) ok = build(tile, k);
         // a region copy still in flight (after a give-up) lands before the CTA exits
         if (pending) mbar_wait_drain(&S.bar[B_ULAND], ucount & 1, status);
         cp_async_wait<0>();

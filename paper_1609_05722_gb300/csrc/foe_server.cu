@@ -154,6 +154,7 @@ foe_status foe_server_create(foe_ctx *ctx, const foe_server_config *cfg, foe_ser
     if (!ctx || !cfg) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(ctx, &cfg->opts, "foe_server_create")) != FOE_OK) return st;
+    if ((st = check_no_tol(ctx, &cfg->opts, "foe_server_create")) != FOE_OK) return st;
     if (cfg->max_active < 1 || cfg->max_active > foe::kMaxBatch || cfg->iters_per_tick < 1 ||
         cfg->hbm_budget_bytes < ((size_t)1 << 20)) {
         set_err(ctx, "server config: need 1 <= max_active <= %d, iters_per_tick >= 1, budget >= 1 MiB",

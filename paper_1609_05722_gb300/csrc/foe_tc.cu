@@ -123,6 +123,7 @@ struct TcSmem {
     int geo[2][5];                                 // image, oy0, ox0, column write range [xs, xe) of the tile in buffer b
     int tprefix[kMaxBatch + 1];                    // the launch's tile prefix, and per image: tiles per row, H, W
     int timg[kMaxBatch][3];
+    int live[kMaxBatch];               // 0 once the image's stopping rule has held (its tiles are skipped)
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -186,6 +187,28 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF, TOH> &S, int qy, int
     return g;
 }
 
+// Image of a tile: a search of the launch's tile table in its copy in shared memory, made at the start of the
+// kernel (parameter-space loads here sat on the staging thread's dependent chain).
+template <bool TF, int TOH>
+__device__ __forceinline__ int tc_image(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int tile)
+{
+    int lo = 0, hi = A.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.tprefix[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The CTA's tiles are c, c + gridDim.x, ... without those of stopped images.
+template <bool TF, int TOH>
+__device__ __forceinline__ int tc_next_live(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int ntiles, int tile)
+{
+    while (tile < ntiles && !S.live[tc_image(A, S, tile)]) tile += gridDim.x;
+    return tile;
+}
+
 // Image, origin and column write range [xs, xe) of a tile.  The horizontal col2im of a response row is formed
 // across the 32 lanes of a warp, so its sums exist only at region columns 0..31.  The padding fold of a pixel
 // within 3 columns of the right border needs the sum at its reflection (up to column W + 2), which lies inside the
@@ -194,19 +217,12 @@ __device__ __forceinline__ float hs_gather(const TcSmem<TF, TOH> &S, int qy, int
 // within 3 of the left border in the first tile (origin 0), whose region holds their reflections, when the flush
 // tile starts at column 1 or 2 (W = 27, 28).  Rows need no such rule: the vertical part of the col2im reads
 // response rows, and the rows that a reflection asks for that lie in the image are always within 3 rows of the
-// output row.  The lookup reads the launch's tile table from its copy in shared memory, made at the start of the
-// kernel: parameter-space loads here sat on the staging thread's dependent chain.
+// output row.
 template <bool TF, int TOH>
 __device__ __forceinline__ void tile_geometry(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int tile, int &im,
                                               int &oy0, int &ox0, int &xe, int &xs)
 {
-    int lo = 0, hi = A.nimg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S.tprefix[mid] <= tile) lo = mid;
-        else hi = mid - 1;
-    }
-    im = lo;
+    im = tc_image(A, S, tile);
     const int tiles_x = S.timg[im][0], W = S.timg[im][2];
     const int lt = tile - S.tprefix[im];
     const int tx = lt % tiles_x;
@@ -388,9 +404,12 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     // once when this launch has no programmatic dependency)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     // an earlier launch that gave up leaves *status set: then do nothing (CTA-uniform decision)
+    // (and the stopping words: tiles of stopped images are skipped)
     if (tid == 0) S.abort_flag = *(volatile int *)status;
+    if (tid < A.nimg) S.live[tid] = !image_stopped(A.img[tid]);
     __syncthreads();
-    if (S.abort_flag) {
+    const int tile0 = tc_next_live(A, S, ntiles, blockIdx.x);
+    if (S.abort_flag || tile0 >= ntiles) {
         if (warp == FWD_WARP) {
             const uint32_t tm = S.tmem_base;
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TMEM_COLS) : "memory");
@@ -401,7 +420,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         mbar_arrive_expect_tx(&S.bar[B_W], WBYTES);
         bulk_g2s(S.Wf, TF ? A.tcops32 : A.tcops, WBYTES, &S.bar[B_W]);
     }
-    stage_input<TF, TOH>(A, S, blockIdx.x, 0, tid, warp, lane);
+    stage_input<TF, TOH>(A, S, tile0, 0, tid, warp, lane);
     stage_operands<MODE, TF, TOH>(A, S, 0, warp, lane);
     cp_async_commit();
     fence_before();
@@ -411,7 +430,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     volatile int *abort_flag = &S.abort_flag;
 
     int k = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    for (int tile = tile0, tn; tile < ntiles; tile = tn, ++k) {
+        tn = tc_next_live(A, S, ntiles, tile + gridDim.x);  // the CTA's next tile
         const int buf = k & 1;
         const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3], xs = S.geo[buf][4];
         const ImgDesc &D = A.img[im];
@@ -423,7 +443,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (k > 0) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();
-        if (tile + (int)gridDim.x < ntiles) stage_input<TF, TOH>(A, S, tile + gridDim.x, buf ^ 1, tid, warp, lane);
+        if (tn < ntiles) stage_input<TF, TOH>(A, S, tn, buf ^ 1, tid, warp, lane);
         cp_async_commit();
 
         // ---- E: built here for the first tile; the expert warps build it for the later ones at the end of the
@@ -553,7 +573,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 }
                 // every forward MMA of this tile is complete (each expert thread saw the last one), so E is free:
                 // the next tile's E is built while the last adjoint and col2im finish
-                if (done && tile + (int)gridDim.x < ntiles &&
+                if (done && tn < ntiles &&
                     mbar_wait(&S.bar[B_UREADY + (buf ^ 1)], ((k + 1) >> 1) & 1, abort_flag, status)) {
                     const float m = region_mean<TOH>(S.U[buf ^ 1], lane);
                     build_e(S, S.U[buf ^ 1], m, 0, kUR<TOH>, tid, 128);
@@ -659,7 +679,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
-        if (tile + (int)gridDim.x < ntiles) stage_operands<MODE, TF, TOH>(A, S, buf ^ 1, warp, lane);
+        if (tn < ntiles) stage_operands<MODE, TF, TOH>(A, S, buf ^ 1, warp, lane);
         cp_async_commit();
     }
 

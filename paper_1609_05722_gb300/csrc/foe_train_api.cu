@@ -25,6 +25,7 @@ extern "C" foe_status foe_train_step(foe_ctx *c, const float *clean, const float
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(c, o, "foe_train_step")) != FOE_OK) return st;
+    if ((st = check_no_tol(c, o, "foe_train_step")) != FOE_OK) return st;
     if (o->model != FOE_MODEL_ANS_L2) { set_err(c, "training needs FOE_MODEL_ANS_L2"); return FOE_EUNSUPPORTED; }
     if (o->prec != FOE_PREC_FP32) { set_err(c, "training runs in FP32"); return FOE_EUNSUPPORTED; }
     if (B < 1 || !dfilters || !dlogalpha) { set_err(c, "need B >= 1 and gradient buffers"); return FOE_EINVAL; }
@@ -174,6 +175,7 @@ extern "C" foe_status foe_train_grad_implicit(foe_ctx *c, const float *clean, co
     if (!c) return FOE_EINVAL;
     foe_status st;
     if ((st = check_opts_fixed(c, o, "foe_train_grad_implicit")) != FOE_OK) return st;
+    if ((st = check_no_tol(c, o, "foe_train_grad_implicit")) != FOE_OK) return st;
     if (o->model != FOE_MODEL_ANS_L2) { set_err(c, "training needs FOE_MODEL_ANS_L2"); return FOE_EUNSUPPORTED; }
     if (o->prec != FOE_PREC_FP32) { set_err(c, "training runs in FP32"); return FOE_EUNSUPPORTED; }
     if (B < 1 || !dfilters || !dlogalpha) { set_err(c, "need B >= 1 and gradient buffers"); return FOE_EINVAL; }

@@ -33,7 +33,7 @@ class foe_prior(C.Structure):
 class foe_solve_opts(C.Structure):
     _fields_ = [("model", C.c_int), ("lam", C.c_float), ("gamma", C.c_float), ("tau", C.c_float),
                 ("tol", C.c_float), ("iters", C.c_int), ("step", C.c_int), ("bc", C.c_int),
-                ("prec", C.c_int), ("zero_c", C.c_float), ("use_graph", C.c_int)]
+                ("prec", C.c_int), ("zero_c", C.c_float), ("use_graph", C.c_int), ("tol_every", C.c_int)]
 
 
 class foe_report(C.Structure):
@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
             "foe_debug_withhold_arrival": (i, [vp]),
             "foe_denoise_binned": (i, [vp, vp, vp, i, i, i, f, C.POINTER(foe_solve_opts), vp, C.POINTER(foe_report)]),
             "foe_denoise_batch": (i, [vp, C.POINTER(foe_image_desc), i, C.POINTER(foe_solve_opts), vp]),
+            "foe_iters_done": (i, [vp, C.POINTER(i), i, vp]),
             "foe_energy_grad": (i, [vp, vp, vp, i, i, i, i, f, i, i, C.POINTER(d), vp, vp]),
             "foe_ipiano_step": (i, [vp, vp, vp, vp, vp, vp, i, i, i, i, f, f, f, i, i, vp]),
             "foe_anscombe": (i, [vp, vp, C.c_long, vp]),
@@ -173,17 +174,18 @@ class SolveOpts:
     prec: int = FOE_PREC_BF16
     zero_c: float = 0.0
     use_graph: bool = False
+    tol_every: int = 10
 
     def c(self) -> foe_solve_opts:
         return foe_solve_opts(self.model, self.lam, self.gamma, self.tau, self.tol, self.iters, self.step,
-                              self.bc, self.prec, self.zero_c, 1 if self.use_graph else 0)
+                              self.bc, self.prec, self.zero_c, 1 if self.use_graph else 0, self.tol_every)
 
 
 def foe_default_opts() -> SolveOpts:
     o = foe_solve_opts()
     _check(lib().foe_default_opts(C.byref(o)))
     return SolveOpts(o.model, o.lam, o.gamma, o.tau, o.tol, o.iters, o.step, o.bc, o.prec, o.zero_c,
-                     bool(o.use_graph))
+                     bool(o.use_graph), o.tol_every)
 
 
 def _prior(filters, alpha):
@@ -276,6 +278,14 @@ def foe_denoise_batch(ctx, descs: list[dict], opts: SolveOpts | None = None, str
         arr[j] = foe_image_desc(_ptr(d["y"]), _ptr(d["x"]), d["H"], d["W"], d["ld"], d["peak"], d["iters"])
     o = (opts or SolveOpts()).c()
     _check(lib().foe_denoise_batch(ctx, arr, len(descs), C.byref(o), _stream(stream)), ctx, "foe_denoise_batch")
+
+
+def foe_iters_done(ctx, n: int = 1, stream=None) -> list[int]:
+    """Iterations taken by each image of the last foe_denoise / foe_denoise_static / foe_denoise_batch solve (the
+    stopping step, or the budget); synchronises the stream."""
+    out = (C.c_int * n)()
+    _check(lib().foe_iters_done(ctx, out, n, _stream(stream)), ctx, "foe_iters_done")
+    return list(out)
 
 
 def foe_energy_grad(ctx, u, data, H: int, W: int, ld: int, model: int, lam: float, bc: int = FOE_BC_SYMMETRIC,
