@@ -129,7 +129,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"foe_tc_step": ("foe_tc.cu", "foe_common.cuh"), "foe_f32_step": ("foe_f32.cu", "foe_common.cuh")}
+KERNEL_SOURCES = {"foe_pair_step": ("foe_pair.cu", "foe_ptx.cuh", "foe_common.cuh"),
+                  "foe_tc_step": ("foe_tc.cu", "foe_ptx.cuh", "foe_common.cuh"),
+                  "foe_f32_step": ("foe_f32.cu", "foe_common.cuh")}
 
 
 def code_only(text: str) -> str:
@@ -161,16 +163,52 @@ def ncu_traffic(kernel_key: str):
     return e.get("bytes_per_launch")
 
 
+# ----------------------------------------------------------------------------- accuracy vs the stored oracle set
+
+def load_golden():
+    """FP64 oracle results of the 512x512 set (written by tests/golden/make_oracle_512.py from the oracle alone):
+    per (model, peak) its PSNR against the clean image and its output at sampled pixels."""
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_512.json")) as f:
+        return json.load(f)
+
+
+def psnr(x, clean, peak) -> float:
+    """10 log10(peak^2 / mean (x - clean)^2), the PSNR of the paper's tables on the [0, peak] scale."""
+    e = np.asarray(x, dtype=np.float64) - np.asarray(clean, dtype=np.float64)
+    return float(10.0 * np.log10(peak * peak / np.mean(e * e)))
+
+
+def accuracy_rows(golden, outputs):
+    """outputs: {(model, peak): H x W output}.  Per case: the oracle's PSNR, this output's PSNR and the difference,
+    and the max |x - x_oracle| over the stored sample of pixels on the [0, 255] scale (255 / peak)."""
+    from paper_1609_05722_gb300 import synth
+    idx = np.array(golden["sample_index"])
+    rows = []
+    for c in golden["cases"]:
+        key = (c["model"], c["peak"])
+        if key not in outputs:
+            continue
+        x = outputs[key]
+        pi = PEAKS.index(c["peak"])
+        clean = synth.clean_image(H, W, 1000 + 10 * pi) * c["peak"]
+        p = psnr(x, clean, c["peak"])
+        rows.append({"model": c["name"], "peak": c["peak"], "psnr_oracle": round(c["psnr_oracle"], 4),
+                     "psnr": round(p, 4), "dpsnr_db": round(p - c["psnr_oracle"], 4),
+                     "max_abs_255": float(np.abs(x.ravel()[idx] - np.array(c["x_sample"])).max() * 255.0 / c["peak"])})
+    return rows
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) timing
 
-def oracle_sample(target_s: float = 12.0):
-    """The FP64 oracle as it stands on the host cores: one 512x512 image, iterations run until ~target_s."""
+def oracle_sample(target_s: float = 12.0, nthreads=None):
+    """The FP64 oracle as it stands on the host cores: one 512x512 image, iterations run until ~target_s
+    (nthreads None: every host core, as the oracle defaults to)."""
     import oracle as O
     from paper_1609_05722_gb300 import synth
     k, a = synth.filter_bank()
     y = synth.poisson_observation(synth.clean_image(H, W, 1000), 4.0, 5000)
     d = O.anscombe(y)
-    pr = O.Problem(k, a, H, W, model=O.MODEL_ANS_L2, lam=1.0, tau=1e-3, gamma=0.8)
+    pr = O.Problem(k, a, H, W, model=O.MODEL_ANS_L2, lam=1.0, tau=1e-3, gamma=0.8, nthreads=nthreads)
     u, up = d.copy(), d.copy()
     t0 = time.perf_counter()
     n = 0
@@ -181,10 +219,11 @@ def oracle_sample(target_s: float = 12.0):
         if time.perf_counter() - t0 >= target_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": H * W * n / dt / 1e6, "unit": "MPix·iter/s", "cores": O.default_threads(),
+    threads = nthreads or O.default_threads()
+    return {"value": H * W * n / dt / 1e6, "unit": "MPix·iter/s", "cores": threads,
             "kind": "oracle",
             "sample": f"FP64 oracle, one 512x512 image (Anscombe quadratic model), {n} iPiano iterations, "
-                      f"{O.default_threads()} threads, {dt:.1f} s"}
+                      f"{threads} threads, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -290,7 +329,7 @@ def run_serving(F, ctx, pool, n_req: int, rate: float, prec: int, budget: int, p
                 size_of[rid] = (H * W, iters)
                 i += 1
             st = F.foe_server_get_stats(srv)
-            if st["queued"] == 0 and st["active"] == 0:
+            if st["queued"] == 0 and st["active"] == 0 and st["finishing"] == 0:
                 if i < len(reqs):
                     time.sleep(max(0.0, reqs[i][0] - (time.perf_counter() - t0)))
                 continue
@@ -363,6 +402,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(12.0)
+        cpu["single_thread"] = oracle_sample(8.0, nthreads=1)
 
     k, a = synth.filter_bank()
     ctx = F.foe_create(k, a)
@@ -388,6 +428,14 @@ def main():
         for lo, model in ((0, F.FOE_MODEL_DIRECT), (5, F.FOE_MODEL_ANS_L2)):
             F.foe_denoise_batch(ctx, descs(xbufs, ybufs, lo, lo + 5), F.SolveOpts(model=model, prec=prec),
                                 stream=stream)
+
+    golden = load_golden() if rank == 0 else None
+
+    def snapshot():
+        """The outputs of the last step, keyed (model, peak), on the host."""
+        torch.cuda.synchronize()
+        return {(int(mi), PEAKS[pi]): xs[5 * mi + pi][:, :W].double().cpu().numpy()
+                for mi in (0, 1) for pi in range(5)}
 
     def timed(prec, steps, warmup):
         for _ in range(warmup):
@@ -427,6 +475,7 @@ def main():
     sampler.start()
     total_ms, loop_ms, launches, pix = timed(prec_main, args.steps, args.warmup)
     clocks = sampler.stop()
+    accuracy = {dtype: accuracy_rows(golden, snapshot())} if golden else None
     pix_iters_step = 10 * H * W * ITERS
     value = job_value(pix_iters_step * args.steps, total_ms / 1e3, world) / 1e6
     ms_per_step = total_ms / args.steps
@@ -435,19 +484,23 @@ def main():
     peaks, peak_src = measured_peaks()
     avg_launch_s = (loop_ms / 1e3) / max(launches, 1)
     pix_per_launch = pix / max(launches, 1)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # the step kernel is timed inside a ~31 ms step of back-to-back launches, not a seconds-long loop: the burst
+    # figure is its denominator
     if prec_main != F.FOE_PREC_FP32:
-        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak = peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained"))
         if prec_main == F.FOE_PREC_TF32:
             peak *= 1.1 / 2.25  # nominal dense TF32 : BF16 rate
-        bound, unit, key = "tensor", "TFLOP/s", "foe_tc_step"
+        bound, unit = "tensor", "TFLOP/s"
+        key = "foe_pair_step" if prec_main == F.FOE_PREC_BF16 else "foe_tc_step"
     else:
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, unit, key = "alu", "TFLOP/s", "foe_f32_step"
     achieved = pix_per_launch * FLOP_PER_PIXEL_ITER / avg_launch_s / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": ncu_traffic(key), "peak_source": f"{peak_src}"
-                + ((" bf16_tflops_sustained" + (" x 1.1/2.25 (nominal tf32:bf16)" if dtype == "tf32" else ""))
-                   if bound == "tensor" else " 152 SMs x 128 FFMA/clk x 2 x sm_max_mhz"),
+                + ((" bf16_tflops (burst)" + (" x 1.1/2.25 (nominal tf32:bf16)" if dtype == "tf32" else ""))
+                   if bound == "tensor" else f" {sms} SMs x 128 FFMA/clk x 2 x sm_max_mhz"),
                 "kernel": key, "avg_launch_us": avg_launch_s * 1e6, "pixels_per_launch": pix_per_launch}
 
     # plain FP32 path on the same workload (the comparison the metric names)
@@ -457,6 +510,8 @@ def main():
         fp32 = {"value": world * pix_iters_step * args.fp32_steps / (t32 / 1e3) / 1e6, "unit": "MPix·iter/s",
                 "ms_per_step": t32 / args.fp32_steps,
                 "avg_launch_us": (l32 / 1e3) / max(n32, 1) * 1e6}
+        if golden:
+            accuracy["f32"] = accuracy_rows(golden, snapshot())
 
     if args.main_only:
         F.foe_destroy(ctx)
@@ -474,6 +529,53 @@ def main():
         t3, l3, n3, p3 = timed(F.FOE_PREC_TF32, args.fp32_steps, 1)
         tf32 = {"value": job_value(pix_iters_step * args.fp32_steps, t3 / 1e3, world) / 1e6, "unit": "MPix·iter/s",
                 "ms_per_step": t3 / args.fp32_steps, "avg_launch_us": (l3 / 1e3) / max(n3, 1) * 1e6}
+        if golden:
+            accuracy["tf32"] = accuracy_rows(golden, snapshot())
+
+    # the I-divergence model (the paper's low-count data term) on the same five images: an accuracy row per
+    # precision, outside the timed workload
+    if golden and not args.main_only:
+        for name, prec in (("bf16", F.FOE_PREC_BF16), ("tf32", F.FOE_PREC_TF32), ("f32", F.FOE_PREC_FP32)):
+            if name not in accuracy:
+                continue
+            F.foe_denoise_batch(ctx, descs(xs, ys, 5, 10), F.SolveOpts(model=F.FOE_MODEL_ANS_IDIV, prec=prec),
+                                stream=stream)
+            torch.cuda.synchronize()
+            outs = {(2, PEAKS[pi]): xs[5 + pi][:, :W].double().cpu().numpy() for pi in range(5)}
+            accuracy[name] += accuracy_rows(golden, outs)
+
+    # the stopping rule (relative change <= 1e-4, checked every 10 steps) on the timed workload: iterations taken
+    # per image and the step time, against the fixed 300-iteration budget
+    stopping = None
+    if not args.main_only:
+        tol, every = 1e-4, 10
+
+        def tol_step():
+            done = []
+            for lo, model in ((0, F.FOE_MODEL_DIRECT), (5, F.FOE_MODEL_ANS_L2)):
+                F.foe_denoise_batch(ctx, descs(xs, ys, lo, lo + 5),
+                                    F.SolveOpts(model=model, prec=prec_main, tol=tol, tol_every=every), stream=stream)
+                done += F.foe_iters_done(ctx, 5, stream=stream)
+            return done
+        for _ in range(3):
+            tol_step()
+        tts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            done = tol_step()
+            e1.record(stream)
+            e1.synchronize()
+            tts.append(e0.elapsed_time(e1))
+        acc_tol = accuracy_rows(golden, snapshot()) if golden else None
+        stopping = {"tol": tol, "tol_every": every, "budget": ITERS,
+                    "iters_done": {f"{m}@{p:g}": n for (m, p), n in
+                                   zip([(m, p) for m in ("direct", "anscombe_l2") for p in PEAKS], done)},
+                    "ms_per_step": float(np.median(tts)), "ms_per_step_fixed_budget": ms_per_step,
+                    "images_per_s": 10 / (float(np.median(tts)) / 1e3),
+                    "accuracy_vs_oracle_300": acc_tol}
 
     # step control by Lipschitz backtracking (FP32, one 512x512 image, 100 iterations, A2 model at peak 8): the
     # host decides every trial, so this leg reports its wall time and the trial counts, not a throughput target
@@ -649,6 +751,8 @@ def main():
             serve["per_request_fp32_prefix"] = run_serving(F, ctx, pool, nb, 200.0, F.FOE_PREC_FP32, 0, 0, False, True)
             serve["per_request_bf16_prefix"] = run_serving(F, ctx, pool, nb, 200.0, prec_main, 0, 0, False, True)
             serve["batched_prefix"] = run_serving(F, ctx, pool, nb, 200.0, prec_main, 40 << 30, 10, True)
+        # the same request mix offered at half the rate (about half the server's capacity): latency without queueing
+        serve["half_rate"] = run_serving(F, ctx, pool, args.serve_requests // 2, 100.0, prec_main, 40 << 30, 10, True)
         del pool
 
     F.foe_destroy(ctx)
@@ -660,7 +764,7 @@ def main():
                 "config": {"workload": CONFIG_NAME, "images_per_step": 10, "H": H, "W": W, "iters": ITERS,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "fp32_plain": fp32, "tf32_tensor_core": tf32, "single_image_ms": float(np.median(lat)),
-                "backtrack": backtrack, "binned": binned,
+                "backtrack": backtrack, "binned": binned, "accuracy": accuracy, "stopping_rule": stopping,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched_uneven_graph": batched, "train": train, "serve": serve,
                 "gpu_launches": per_step_launches * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -313,6 +313,7 @@ typedef struct {
 
 typedef struct {
     int queued, active;       /* waiting for admission / admitted and iterating */
+    int finishing;            /* finished in the last round, completed by the next foe_server_tick */
     long long completed, ticks, launches;
     double pixel_iters;       /* pixel-iterations executed so far */
     size_t bytes_in_use, bytes_peak, bytes_budget;
@@ -329,9 +330,16 @@ FOE_API void foe_server_destroy(foe_server *srv);
 FOE_API foe_status foe_server_submit(foe_server *srv, const float *y_host, int y_pitch, float *x_host, int x_pitch,
                                      int H, int W, float peak, int iters, long long *id_out);
 /* One scheduling round: admit queued requests in FIFO order while a slot and arena memory are free
- * (upload + initialise them), advance every admitted request by up to iters_per_tick iterations, then
- * finish the requests whose budget is spent (output map, copy to x_host, memory returned).  Returns
- * after the round's device work is complete; *n_completed (nullable) = requests finished this tick. */
+ * (upload + initialise them), advance every admitted request by up to iters_per_tick iterations, and
+ * queue the finishing of the requests whose budget is then spent (output map, copy to x_host).  Rounds
+ * are pipelined: the call queues this round's device work behind the previous round's and then waits
+ * for the previous round only, whose finished requests it completes (memory returned, ids to poll,
+ * x_host written); *n_completed (nullable) = requests completed by this call.  A request finishing in
+ * round k is therefore reported by the call of round k + 1; a call with nothing to admit or iterate
+ * only completes the previous round (stats.finishing counts the requests it would complete).
+ * If a device-side wait of the step kernel expired (FOE_ETIMEOUT), the server stops: this and every
+ * later tick return FOE_ETIMEOUT, the affected requests are never reported, and the caller destroys
+ * the server and reads (and clears) the context's status with foe_device_status. */
 FOE_API foe_status foe_server_tick(foe_server *srv, int *n_completed);
 /* Ids of completed requests not yet polled (up to max_ids), oldest first. */
 FOE_API foe_status foe_server_poll(foe_server *srv, long long *ids, int max_ids, int *n);

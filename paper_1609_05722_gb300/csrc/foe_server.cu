@@ -9,6 +9,11 @@
 // is spent: output map, copy back, memory returned to the arena.  Requests that arrive while others
 // are iterating join at the next tick: that is the continuous batching.  Every request's iterate state
 // stays on the device from admission to completion.
+//
+// Ticks are pipelined: tick k queues its work behind tick k - 1's on the server's stream and only then waits
+// for tick k - 1 (an event), so the host's admission, uploads and graph update for tick k overlap tick k - 1 on
+// the GPU and the GPU does not idle between ticks.  A request that finishes in tick k is reported (and its memory
+// returned) by tick k + 1; a tick with nothing left to admit or iterate only completes the previous one.
 #include <deque>
 #include <map>
 
@@ -92,9 +97,14 @@ struct foe_server {
     char *arena_base = nullptr;
     Arena arena;
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};  // tick k uses exec[k & 1]: the one being updated is idle
+    cudaEvent_t done_ev[2] = {nullptr, nullptr};   // end of tick k's device work: done_ev[k & 1]
+    int *h_status = nullptr;                       // pinned [2]: the context's device status after tick k
     std::deque<Request *> queue;
     std::vector<Request *> active;
+    std::vector<Request *> finishing;              // finished in the last queued tick, not yet complete
+    bool pending = false;                          // a queued tick not yet waited for
+    foe_status failed = FOE_OK;                    // sticky: a device wait expired in some tick
     std::vector<long long> completed_ids;
     long long next_id = 1, completed = 0, ticks = 0, launches = 0;
     double pixel_iters = 0.0;
@@ -168,7 +178,10 @@ foe_status foe_server_create(foe_ctx *ctx, const foe_server_config *cfg, foe_ser
     sv->tau = cfg->opts.tau > 0.0f ? cfg->opts.tau : default_tau(ctx->symbol_max, cfg->opts.bc, cfg->opts.gamma);
     cudaError_t e;
     if ((e = cudaMalloc(&sv->arena_base, cfg->hbm_budget_bytes)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&sv->done_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&sv->done_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaHostAlloc(&sv->h_status, 2 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess) {
         set_err(ctx, "server create: %s", cudaGetErrorString(e));
         foe_server_destroy(sv);
         return e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA;
@@ -182,11 +195,16 @@ void foe_server_destroy(foe_server *sv)
 {
     if (!sv) return;
     if (sv->stream) cudaStreamSynchronize(sv->stream);
-    if (sv->exec) cudaGraphExecDestroy(sv->exec);
+    for (cudaGraphExec_t x : sv->exec)
+        if (x) cudaGraphExecDestroy(x);
+    for (cudaEvent_t e : sv->done_ev)
+        if (e) cudaEventDestroy(e);
+    if (sv->h_status) cudaFreeHost(sv->h_status);
     if (sv->stream) cudaStreamDestroy(sv->stream);
     cudaFree(sv->arena_base);
     for (Request *r : sv->queue) delete r;
     for (Request *r : sv->active) delete r;
+    for (Request *r : sv->finishing) delete r;
     delete sv;
 }
 
@@ -228,6 +246,33 @@ foe_status foe_server_submit(foe_server *sv, const float *y_host, int y_pitch, f
     return FOE_OK;
 }
 
+// Waits for the queued tick, then completes its finished requests (memory back to the arena, ids to poll).
+static foe_status complete_pending(foe_server *sv, int *n_completed)
+{
+    foe_ctx *c = sv->ctx;
+    if (!sv->pending) return FOE_OK;
+    const int slot = (int)((sv->ticks - 1) & 1);
+    FOE_CUDA(c, cudaEventSynchronize(sv->done_ev[slot]));
+    sv->pending = false;
+    if (sv->h_status[slot] != 0) {
+        // the tick's results are not valid: the server stops here (every later call returns this status); its
+        // requests stay owned by it until foe_server_destroy, and the context's status is left for
+        // foe_device_status to read and clear
+        sv->failed = (foe_status)sv->h_status[slot];
+        set_err(c, "a device-side wait expired during a server tick; the server has stopped");
+        return sv->failed;
+    }
+    for (Request *r : sv->finishing) {
+        sv->arena.release(r->off, r->bytes);
+        sv->completed_ids.push_back(r->id);
+        sv->completed++;
+        delete r;
+    }
+    if (n_completed) *n_completed = (int)sv->finishing.size();
+    sv->finishing.clear();
+    return FOE_OK;
+}
+
 foe_status foe_server_tick(foe_server *sv, int *n_completed)
 {
     NvtxRange nvtx_range("foe_server_tick");
@@ -235,7 +280,14 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
     foe_ctx *c = sv->ctx;
     const foe_solve_opts &o = sv->cfg.opts;
     foe_status st;
-    // 1. admission: FIFO order, while a slot and arena memory are free
+    if (n_completed) *n_completed = 0;
+    if (sv->failed != FOE_OK) {
+        set_err(c, "the server stopped after an expired device-side wait; destroy it");
+        return sv->failed;
+    }
+    if (sv->queue.empty() && sv->active.empty()) return complete_pending(sv, n_completed);
+    // 1. admission: FIFO order, while a slot and arena memory are free (the memory of the requests that finish
+    // in the queued tick comes back when it completes, below)
     while (!sv->queue.empty() && (int)sv->active.size() < sv->cfg.max_active) {
         Request *r = sv->queue.front();
         size_t off;
@@ -249,7 +301,21 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
         FOE_CUDA(c, foe::launch_init(sl.d, r->H, r->W, r->ld, r->ld, r->model, o.zero_c, sl.d, sl.uh0, lo_plane(o.prec, sl.ul), sl.delta,
                                      sv->stream));
     }
+    if (sv->active.empty()) {
+        // nothing fits until the queued tick's memory comes back (with nothing queued on the device the whole
+        // arena is free and the first request fits, so this retries once)
+        if (!sv->pending) {
+            set_err(c, "server: no request fits the free arena");
+            return FOE_ENOMEM;
+        }
+        if ((st = complete_pending(sv, n_completed)) != FOE_OK) return st;
+        int more = 0;
+        st = sv->queue.empty() ? FOE_OK : foe_server_tick(sv, &more);
+        if (n_completed) *n_completed += more;
+        return st;
+    }
     // 2. iterations of every admitted request
+    const int slot = (int)(sv->ticks & 1);
     if (sv->cfg.use_graphs) {
         FOE_CUDA(c, cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal));
         st = enqueue_iterations(sv);
@@ -260,25 +326,27 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
             return st;
         }
         FOE_CUDA(c, ec);
+        // exec[slot] was last launched two ticks ago, which has completed
+        cudaGraphExec_t &exec = sv->exec[slot];
         bool updated = false;
-        if (sv->exec) {
+        if (exec) {
             cudaGraphExecUpdateResultInfo info;
-            updated = cudaGraphExecUpdate(sv->exec, graph, &info) == cudaSuccess;
+            updated = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
             if (!updated) {
                 (void)cudaGetLastError();
-                cudaGraphExecDestroy(sv->exec);
-                sv->exec = nullptr;
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
             }
         }
         if (!updated) {
-            const cudaError_t ei = cudaGraphInstantiate(&sv->exec, graph, 0);
+            const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
             if (ei != cudaSuccess) {
                 cudaGraphDestroy(graph);
                 FOE_CUDA(c, ei);
             }
         }
         cudaGraphDestroy(graph);
-        FOE_CUDA(c, cudaGraphLaunch(sv->exec, sv->stream));
+        FOE_CUDA(c, cudaGraphLaunch(exec, sv->stream));
     } else if ((st = enqueue_iterations(sv)) != FOE_OK) {
         return st;
     }
@@ -297,23 +365,15 @@ foe_status foe_server_tick(foe_server *sv, int *n_completed)
                                       r->W * sizeof(float), r->H, cudaMemcpyDeviceToHost, sv->stream));
         finished.push_back(r);
     }
-    FOE_CUDA(c, cudaStreamSynchronize(sv->stream));
-    int dev_status = 0;
-    FOE_CUDA(c, cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (dev_status) {
-        set_err(c, "a device-side wait expired during a server tick");
-        return (foe_status)dev_status;
-    }
-    for (Request *r : finished) {
-        sv->arena.release(r->off, r->bytes);
-        sv->completed_ids.push_back(r->id);
-        sv->completed++;
-        delete r;
-    }
+    FOE_CUDA(c, cudaMemcpyAsync(sv->h_status + slot, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, sv->stream));
+    FOE_CUDA(c, cudaEventRecord(sv->done_ev[slot], sv->stream));
     sv->active.swap(still);
+    // 4. the previous tick (queued before this one) completes while this one runs
+    st = complete_pending(sv, n_completed);
+    sv->finishing.insert(sv->finishing.end(), finished.begin(), finished.end());
+    sv->pending = true;
     sv->ticks++;
-    if (n_completed) *n_completed = (int)finished.size();
-    return FOE_OK;
+    return st;
 }
 
 foe_status foe_server_poll(foe_server *sv, long long *ids, int max_ids, int *n)
@@ -331,6 +391,7 @@ foe_status foe_server_get_stats(const foe_server *sv, foe_server_stats *s)
     if (!sv || !s) return FOE_EINVAL;
     s->queued = (int)sv->queue.size();
     s->active = (int)sv->active.size();
+    s->finishing = (int)sv->finishing.size();
     s->completed = sv->completed;
     s->ticks = sv->ticks;
     s->launches = sv->launches;

@@ -52,8 +52,8 @@ class foe_server_config(C.Structure):
 
 
 class foe_server_stats(C.Structure):
-    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("completed", C.c_longlong), ("ticks", C.c_longlong),
-                ("launches", C.c_longlong), ("pixel_iters", C.c_double), ("bytes_in_use", C.c_size_t),
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("finishing", C.c_int), ("completed", C.c_longlong),
+                ("ticks", C.c_longlong), ("launches", C.c_longlong), ("pixel_iters", C.c_double), ("bytes_in_use", C.c_size_t),
                 ("bytes_peak", C.c_size_t), ("bytes_budget", C.c_size_t)]
 
 

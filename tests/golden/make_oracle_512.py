@@ -1,7 +1,8 @@
 """Writes tests/golden/oracle_512.json: FP64 oracle results for the 512x512 benchmark set.
 
 The set is the paper's noise levels at the benchmark size: peaks {1, 2, 4, 8, 30} x {direct model,
-Anscombe quadratic model}, 300 iPiano iterations, the seeded synthetic bank and images.  For each
+Anscombe quadratic model, Anscombe I-divergence model}, 300 iPiano iterations, the seeded synthetic bank
+and images.  For each
 case it stores the oracle's PSNR against the clean image, a sample of output pixels, and a hash of
 the inputs (so that a test can tell whether the generator still produces the same images).  It
 calls only the oracle and the seeded input generator.
@@ -24,7 +25,7 @@ from paper_1609_05722_gb300 import synth  # noqa: E402
 H = W = 512
 ITERS = 300
 PEAKS = (1.0, 2.0, 4.0, 8.0, 30.0)
-MODELS = ((0, "direct"), (1, "anscombe_l2"))
+MODELS = ((0, "direct"), (1, "anscombe_l2"), (2, "anscombe_idiv"))
 GAMMA = float(np.float32(0.8))
 LAM = 1.0
 NSAMPLE = 512

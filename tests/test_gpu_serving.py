@@ -118,3 +118,34 @@ def test_request_larger_than_budget_is_refused(ctx):
         assert e.value.status == F.FOE_ENOMEM
     finally:
         F.foe_server_destroy(srv)
+
+
+def test_expired_device_wait_stops_the_server(ctx):
+    """A bounded device wait made to expire (one withheld mbarrier arrival, no GPU fault): the tick that completes
+    the affected round reports FOE_ETIMEOUT, every later tick returns it without device work, no affected request
+    is reported, and after foe_device_status a new server on the same context serves bit-exact results."""
+    ys = images()
+    srv = F.foe_server_create(ctx, 64 << 20, 4, 5, True, F.SolveOpts(model=F.FOE_MODEL_AUTO, prec=F.FOE_PREC_BF16))
+    outs = [torch.zeros((H, W)).pin_memory() for H, W, _, _ in REQS]
+    try:
+        for j in (0, 2):
+            H, W, peak, it = REQS[j]
+            F.foe_server_submit(srv, ys[j], outs[j], H, W, peak, it, ctx=ctx)
+        F.foe_debug_withhold_arrival(ctx)
+        F.foe_server_tick(srv, ctx)                      # queues the affected round
+        with pytest.raises(F.FoeError) as e:
+            for _ in range(3):
+                F.foe_server_tick(srv, ctx)              # completes it
+        assert e.value.status == F.FOE_ETIMEOUT
+        with pytest.raises(F.FoeError) as e:
+            F.foe_server_tick(srv, ctx)
+        assert e.value.status == F.FOE_ETIMEOUT
+        assert F.foe_server_poll(srv) == []
+    finally:
+        F.foe_server_destroy(srv)
+    assert F.foe_device_status(ctx) == F.FOE_ETIMEOUT
+    assert F.foe_device_status(ctx) == F.FOE_OK
+    out, _, _ = serve(ctx, ys, [(0, 0), (2, 0)], F.FOE_PREC_BF16, 64 << 20, 4, 5, True)
+    refs = reference(ctx, ys, F.FOE_PREC_BF16)
+    for j in out:
+        assert np.array_equal(out[j], refs[j])

@@ -152,12 +152,15 @@ def _golden():
         return json.load(f)
 
 
-@pytest.mark.parametrize("case", range(10))
+@pytest.mark.parametrize("case", range(15))
 def test_tc_512_psnr_vs_oracle(dev, ctx, bank32, case):
-    """The benchmark set: 512x512, 300 iterations, peaks {1,2,4,8,30} x {direct, Anscombe-L2}.
+    """The benchmark set: 512x512, 300 iterations, peaks {1,2,4,8,30} x {direct, Anscombe-L2, Anscombe-I-divergence}.
 
     Oracle values come from tests/golden/make_oracle_512.py (oracle only); if the generator no
-    longer reproduces the stored inputs the oracle is rerun here."""
+    longer reproduces the stored inputs the oracle is rerun here.  Bars: PSNR within 0.02 dB of the oracle's for
+    BF16 and TF32 (the metric's bar); sampled max-abs on the [0, 255] scale <= 1e-4 for FP32 and <= 1 grey level
+    for BF16, about twice the largest BF16 figure measured on this set (0.55, direct model at peak 30), so that a
+    localised artefact cannot hide inside a PSNR average."""
     g = _golden()
     c = g["cases"][case]
     H, W, peak, model = g["H"], g["W"], c["peak"], c["model"]
@@ -193,3 +196,4 @@ def test_tc_512_psnr_vs_oracle(dev, ctx, bank32, case):
           f"sampled max-abs fp32 {err32:.2e}, bf16 {errbf:.2e}")
     assert dp <= 0.02 and dp32 <= 0.02
     assert err32 <= 1e-4
+    assert errbf <= 1.0
