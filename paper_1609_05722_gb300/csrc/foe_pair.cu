@@ -20,9 +20,10 @@
 //            3 packed adds for two pixels); vertical: a register carry over the rows of each lane quarter, stored as
 //            four FP16 partial rows per output row, summed in FP32 in the output pass.
 //
-// Roles (24 warps): 0-11 expert (warp w: TMEM lane quarter w % 4, response columns 32 (w / 4) .. + 31, a third
-// of the 96 of a pair), 12-15 col2im (lane quarter w % 4),
-// 16 forward MMA issue, 17 adjoint MMA issue, 18-21 output pass, 22-23 staging.  The staging warps copy in the next
+// Roles (20 warps): 0-7 expert (warp w: TMEM lane quarter w % 4, response columns 48 (w / 4) .. + 47, one pixel of
+// the pair), 8-11 col2im (lane quarter w % 4), 12 forward MMA issue, 13 adjoint MMA issue, 14-17 output pass,
+// 18-19 staging.  (12 expert warps of 32 columns measured 52.8 us per 5 x 512^2 launch, 8 of 48 columns 50.9 us,
+// 4 of 96 columns 51.2 us.)  The staging warps copy in the next
 // tile's input region (one TMA box; for border tiles under symmetric padding the reflected ring is then filled in
 // from the box) and build its E operand (double-buffered) while the current tile runs; the output warps run the
 // output pass (padding fold, iPiano step) of the current tile row by row as the col2im warps finish its M-tiles,
@@ -84,8 +85,8 @@ constexpr int kORing = 4;            // output-pass operands are copied in kORin
 
 // mbarriers
 constexpr int B_FWD = 0;      // [3] forward MMAs of M-tile g complete: R(g) ready           count 1 (commit)
-constexpr int B_RFREE = 3;    // [3] R(g) loaded by every expert thread: the R stage is free  count 384
-constexpr int B_PSI = 6;      // [NPST] Psi(g) in tensor memory (every expert thread)         count 384
+constexpr int B_RFREE = 3;    // [3] R(g) loaded by every expert thread: the R stage is free  count 32 NEXP
+constexpr int B_PSI = 6;      // [NPST] Psi(g) in tensor memory (every expert thread)         count 32 NEXP
 constexpr int B_PFREE = 9;    // [NPST] adjoint MMAs of g complete: the Psi stage is free     count 1 (commit)
 constexpr int B_ADJ = 12;     // [NZST] adjoint MMAs of g complete: Z2(g) ready                count 1 (commit)
 constexpr int B_ZFREE = 15;   // [NZST] Z2(g) loaded by every col2im thread                   count 128

@@ -131,3 +131,43 @@ def test_lbfgs_training_with_the_implicit_gradient_decreases_the_loss(setup):
                                           torch.from_numpy(np.log(a.astype(np.float64))), max_iter=3, tol=0.0)
     print(f"L-BFGS (implicit gradient) losses {[round(x, 4) for x in losses]} ({reason})")
     assert losses[1] < losses[0] and min(losses) < 0.999 * losses[0]
+
+
+def test_lbfgs_on_the_device_follows_the_oracle_driven_trajectory(setup):
+    # Algorithm 1 driven by the device's loss and implicit gradient against the same driver given the FP64 oracle's
+    # (6 filters, two 8x9 images at peak 4, 400 inner iterations, the step of each evaluation's filters): the losses
+    # of the iterations agree to 1e-4 relative and the parameters end within 1 % of the distance they moved.
+    from paper_1609_05722_gb300.train import FoEImplicitLoss, lbfgs_train
+    k, a, _ = setup
+    NF, H, W, Bn, T = 6, 8, 9, 2, 400
+    clean, noisy, cd, nd, ld = batch(Bn, H, W, 4.0, 70)
+
+    class OracleLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, kt, lat):
+            kk = kt.detach().numpy()
+            aa = np.exp(lat.detach().numpy())
+            tau = 0.99 * 2 * (1 - GAMMA) / (O.lipschitz(kk, aa) + 2e-3)
+            pr = O.Problem(kk, aa, H, W, model=O.MODEL_ANS_L2, lam=1.0, tau=tau, gamma=GAMMA, nthreads=1)
+            L, dk, da, _, _ = pr.train_grad_implicit(clean, noisy, T, 500, 1e-10)
+            ctx.save_for_backward(torch.from_numpy(dk), torch.from_numpy(da))
+            return torch.tensor(L, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            dk, da = ctx.saved_tensors
+            return g * dk, g * da
+
+    def device_loss(kt, lat):
+        return FoEImplicitLoss.apply(kt, lat, cd, nd, T, 1.0, GAMMA, 0.0, 500, 1e-5, W)
+
+    k0 = torch.from_numpy(k[:NF].astype(np.float64)).view(NF, 7, 7)
+    la0 = torch.from_numpy(np.log(a[:NF].astype(np.float64)))
+    kd, lad, Ld, rd = lbfgs_train(device_loss, k0.clone(), la0.clone(), max_iter=3, tol=0.0)
+    ko, lao, Lo, ro = lbfgs_train(OracleLoss.apply, k0.clone(), la0.clone(), max_iter=3, tol=0.0)
+    print(f"L-BFGS device {[round(x, 6) for x in Ld]} ({rd}), oracle {[round(x, 6) for x in Lo]} ({ro})")
+    assert rd == ro == "max_iter" and len(Ld) == len(Lo) == 4
+    np.testing.assert_allclose(Ld, Lo, rtol=1e-4)
+    assert Lo[-1] < 0.99 * Lo[0]
+    assert torch.linalg.vector_norm(kd - ko) <= 1e-2 * torch.linalg.vector_norm(ko - k0)
+    assert torch.linalg.vector_norm(lad - lao) <= 1e-2 * torch.linalg.vector_norm(lao - la0)
