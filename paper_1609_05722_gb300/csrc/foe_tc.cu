@@ -55,14 +55,11 @@ constexpr int TO = 26;                 // output tile width
 constexpr int RS = TO + 6;             // response region width = 32 = warp width
 constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 used)
 
-// Tile height (per image, chosen by the host): BF16 images of at least 232 rows use 26 x 58 tiles (16 M-tiles),
-// which repeat the 3-row response ring less often and amortise each tile's E build, output pass and barriers over
-// more M-tiles; smaller images, and the TF32 path, use 26 x 26 tiles, which keep more SMs busy on small work.  The
-// height is a template parameter of the kernel, and a launch whose images use both heights runs as two kernel
-// launches, one per height.  An image is tiled the same way whatever else shares its launch, so its result does not
-// depend on the batch.  Two CTAs still fit an SM with the tall tiles because the horizontal col2im sums are kept in
-// FP16 on the BF16 path (their magnitude stays far below its range, and its 11-bit significand is finer than the
-// BF16 rounding of u and psi); TF32 keeps FP32 sums and its ~4x smaller error.
+// Tile height: 26 (the instance built here; the kernel keeps it a template parameter).  This kernel runs the TF32
+// path and BF16 images of fewer than 59 rows; larger BF16 images go to the pixel-pair kernel (foe_pair.cu).  An
+// image is tiled the same way whatever else shares its launch, so its result does not depend on the batch.  The
+// horizontal col2im sums are kept in FP16 on the BF16 path (their magnitude stays far below its range, and its
+// 11-bit significand is finer than the BF16 rounding of u and psi); TF32 keeps FP32 sums and its ~4x smaller error.
 constexpr int kShortH = 26;
 template <bool TF>
 struct HsType {

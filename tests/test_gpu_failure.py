@@ -61,7 +61,7 @@ def test_an_expired_device_wait_is_reported_and_the_context_recovers(ctx):
 
 @pytest.mark.parametrize("prec", [F.FOE_PREC_FP32, F.FOE_PREC_BF16])
 def test_resume_from_a_host_checkpoint_is_bitwise_identical(ctx, prec, tmp_path):
-    H, W, n = 300, 70, 12   # 300 rows: 26 x 58 tiles on the BF16 path
+    H, W, n = 300, 70, 12   # 300 rows: the pixel-pair kernel's 58 x 58 tiles on the BF16 path
     ld = (W + 3) // 4 * 4
     y = synth.poisson_observation(synth.clean_image(H, W, 41), 4.0, 42)
     v = 2.0 * np.sqrt(y + 3.0 / 8.0)
