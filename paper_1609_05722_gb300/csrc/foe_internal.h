@@ -303,10 +303,10 @@ inline foe::StepConsts step_consts(float tau, float gamma, float lambda)
     return s;
 }
 
-inline void tile_dims(int prec, int H, int &th, int &tw)
+inline void tile_dims(int prec, int H, int W, int &th, int &tw)
 {
     if (prec == FOE_PREC_BF16 || prec == FOE_PREC_TF32) {
-        th = foe::tc_tile_h(prec == FOE_PREC_TF32, H);
+        th = foe::tc_tile_h(prec == FOE_PREC_TF32, H, W);
         tw = foe::tc_tile_w(th);
     } else {
         th = tw = foe::f32_tile();
@@ -335,7 +335,7 @@ inline void args_add(foe_ctx *c, int prec, const ImgDesc &d)
 {
     LaunchArgs &A = c->args;
     int th, tw;
-    tile_dims(prec, d.H, th, tw);
+    tile_dims(prec, d.H, d.W, th, tw);
     ImgDesc e = d;
     e.tiles_x = (d.W + tw - 1) / tw;
     e.tile_h = th;

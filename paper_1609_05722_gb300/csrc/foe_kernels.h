@@ -14,14 +14,15 @@ cudaError_t f32_setup();
 cudaError_t f32_launch(const LaunchArgs &a, int mode, cudaStream_t s);
 
 // Tensor-core (tcgen05, BF16 or TF32) fused tile kernels: 26 x 26 tiles (foe_tc.cu) and 58 x 58 pixel-pair tiles
-// (foe_pair.cu, BF16 images of at least pair_min_rows() rows).  tc_launch runs the images of a launch in the
-// kernel their tiles belong to.
-int tc_tile_h(bool tf32, int H);  // output rows of the tensor-core tiles of an image of H rows
+// (foe_pair.cu, BF16 images of at least pair_min_rows() rows and pair_min_pixels() pixels).  tc_launch runs the
+// images of a launch in the kernel their tiles belong to.
+int tc_tile_h(bool tf32, int H, int W);  // output rows of the tensor-core tiles of an H x W image
 int tc_tile_w(int tile_h);        // output columns of those tiles
 cudaError_t tc_setup();
 cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s);
 int pair_tile();
 int pair_min_rows();
+long pair_min_pixels();
 cudaError_t pair_setup();
 // the images of `a` tiled pair_tile() x pair_tile() (all of them if `all`), one persistent CTA per SM
 cudaError_t pair_launch(const LaunchArgs &a, int mode, bool all, int sms, int *d_status, cudaStream_t s);

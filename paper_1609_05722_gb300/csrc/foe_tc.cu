@@ -56,7 +56,7 @@ constexpr int RS = TO + 6;             // response region width = 32 = warp widt
 constexpr int UC = RS + 8;             // floats per input-region row (RS + 7 used)
 
 // Tile height: 26 (the instance built here; the kernel keeps it a template parameter).  This kernel runs the TF32
-// path and BF16 images of fewer than 59 rows; larger BF16 images go to the pixel-pair kernel (foe_pair.cu).  An
+// path and BF16 images below the pixel-pair kernel's size (tc_tile_h); larger BF16 images go to that kernel.  An
 // image is tiled the same way whatever else shares its launch, so its result does not depend on the batch.  The
 // horizontal col2im sums are kept in FP16 on the BF16 path (their magnitude stays far below its range, and its
 // 11-bit significand is finer than the BF16 rounding of u and psi); TF32 keeps FP32 sums and its ~4x smaller error.
@@ -121,6 +121,7 @@ struct TcSmem {
     int tprefix[kMaxBatch + 1];                    // the launch's tile prefix, and per image: tiles per row, H, W
     int timg[kMaxBatch][3];
     int live[kMaxBatch];               // 0 once the image's stopping rule has held (its tiles are skipped)
+    int tnext[2];                      // the CTA's tile after the tile in buffer b (>= ntiles: none)
     uint64_t bar[NBAR];
     uint32_t tmem_base;
     int abort_flag;
@@ -200,7 +201,7 @@ __device__ __forceinline__ int tc_image(const LaunchArgs &A, const TcSmem<TF, TO
 
 // The CTA's tiles are c, c + gridDim.x, ... without those of stopped images.
 template <bool TF, int TOH>
-__device__ __forceinline__ int tc_next_live(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int ntiles, int tile)
+__device__ __noinline__ int tc_next_live(const LaunchArgs &A, const TcSmem<TF, TOH> &S, int ntiles, int tile)
 {
     while (tile < ntiles && !S.live[tc_image(A, S, tile)]) tile += gridDim.x;
     return tile;
@@ -406,6 +407,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     if (tid < A.nimg) S.live[tid] = !image_stopped(A.img[tid]);
     __syncthreads();
     const int tile0 = tc_next_live(A, S, ntiles, blockIdx.x);
+    if (tid == 0) S.tnext[0] = tc_next_live(A, S, ntiles, tile0 + (int)gridDim.x);  // read after the barrier below
     if (S.abort_flag || tile0 >= ntiles) {
         if (warp == FWD_WARP) {
             const uint32_t tm = S.tmem_base;
@@ -427,8 +429,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
     volatile int *abort_flag = &S.abort_flag;
 
     int k = 0;
-    for (int tile = tile0, tn; tile < ntiles; tile = tn, ++k) {
-        tn = tc_next_live(A, S, ntiles, tile + gridDim.x);  // the CTA's next tile
+    // the CTA's next tile is kept in shared memory (S.tnext[buf], written by thread 0 one tile ahead): a value
+    // kept live in registers across the tile made the kernel spill
+    for (int tile = tile0; tile < ntiles; tile = S.tnext[k & 1], ++k) {
         const int buf = k & 1;
         const int im = S.geo[buf][0], oy0 = S.geo[buf][1], ox0 = S.geo[buf][2], xe = S.geo[buf][3], xs = S.geo[buf][4];
         const ImgDesc &D = A.img[im];
@@ -440,7 +443,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         if (k > 0) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();
-        if (tn < ntiles) stage_input<TF, TOH>(A, S, tn, buf ^ 1, tid, warp, lane);
+        if (tid == 0) {
+            const int tn = S.tnext[buf];
+            S.tnext[buf ^ 1] = tn < ntiles ? tc_next_live(A, S, ntiles, tn + (int)gridDim.x) : ntiles;
+        }
+        if (const int tn = S.tnext[buf]; tn < ntiles) stage_input<TF, TOH>(A, S, tn, buf ^ 1, tid, warp, lane);
         cp_async_commit();
 
         // ---- E: built here for the first tile; the expert warps build it for the later ones at the end of the
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 }
                 // every forward MMA of this tile is complete (each expert thread saw the last one), so E is free:
                 // the next tile's E is built while the last adjoint and col2im finish
-                if (done && tn < ntiles &&
+                if (done && S.tnext[buf] < ntiles &&
                     mbar_wait(&S.bar[B_UREADY + (buf ^ 1)], ((k + 1) >> 1) & 1, abort_flag, status)) {
                     const float m = region_mean<TOH>(S.U[buf ^ 1], lane);
                     build_e(S, S.U[buf ^ 1], m, 0, kUR<TOH>, tid, 128);
@@ -676,7 +683,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
         // Hs and this tile's buffers are reused by the next tiles
         __syncthreads();
         if (*abort_flag) break;
-        if (tn < ntiles) stage_operands<MODE, TF, TOH>(A, S, buf ^ 1, warp, lane);
+        if (S.tnext[buf] < ntiles) stage_operands<MODE, TF, TOH>(A, S, buf ^ 1, warp, lane);
         cp_async_commit();
     }
 
@@ -735,7 +742,16 @@ cudaError_t tc_attr()
 
 }  // namespace
 
-int tc_tile_h(bool tf32, int H) { return !tf32 && H >= pair_min_rows() ? pair_tile() : kShortH; }
+// BF16 images of at least pair_min_rows() rows and pair_min_pixels() pixels take the pixel-pair kernel's 58 x 58 tiles;
+// the rest take 26 x 26 tiles.  The pair kernel runs one CTA per SM and a tile in about 20 us; the 26 x 26 kernel
+// runs two CTAs per SM and a tile in about 10 us, so it finishes small images sooner (300 iterations: 384^2 alone
+// 3.9 ms against 7.1 ms) while the pair kernel does more per SM once an image fills the GPU (five 512^2 images
+// together: 15.8 ms against 19.5 ms; five 384^2: 11.6 against 11.8 ms).  The choice depends on the image alone, so an
+// image is tiled, and rounded, the same way in any batch.
+int tc_tile_h(bool tf32, int H, int W)
+{
+    return !tf32 && H >= pair_min_rows() && (long)H * W >= pair_min_pixels() ? pair_tile() : kShortH;
+}
 int tc_tile_w(int tile_h) { return tile_h == pair_tile() ? pair_tile() : TO; }
 
 cudaError_t tc_setup()

@@ -35,8 +35,9 @@ def _image(H, W, seed):
     return torch.from_numpy(y.astype(np.float32)).cuda()
 
 
-def test_an_expired_device_wait_is_reported_and_the_context_recovers(ctx):
-    H = W = 64
+@pytest.mark.parametrize("side", [64, 456])   # the 26 x 26 kernel, the pixel-pair kernel
+def test_an_expired_device_wait_is_reported_and_the_context_recovers(ctx, side):
+    H = W = side
     y = _image(H, W, 31)
     opts = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_BF16, iters=10)
     ref = torch.zeros_like(y)
@@ -61,7 +62,7 @@ def test_an_expired_device_wait_is_reported_and_the_context_recovers(ctx):
 
 @pytest.mark.parametrize("prec", [F.FOE_PREC_FP32, F.FOE_PREC_BF16])
 def test_resume_from_a_host_checkpoint_is_bitwise_identical(ctx, prec, tmp_path):
-    H, W, n = 300, 70, 12   # 300 rows: the pixel-pair kernel's 58 x 58 tiles on the BF16 path
+    H, W, n = 300, 700, 12   # 210000 pixels: the pixel-pair kernel's 58 x 58 tiles on the BF16 path
     ld = (W + 3) // 4 * 4
     y = synth.poisson_observation(synth.clean_image(H, W, 41), 4.0, 42)
     v = 2.0 * np.sqrt(y + 3.0 / 8.0)

@@ -119,7 +119,7 @@ def test_fp32_stops_where_the_oracle_stops(dev, ctx, bank32, model, peak, every)
     assert np.abs(x - ref).max() * 255.0 / peak <= 1e-4
 
 
-@pytest.mark.parametrize("prec,shape", [(F.FOE_PREC_BF16, (128, 150)), (F.FOE_PREC_BF16, (40, 50)),
+@pytest.mark.parametrize("prec,shape", [(F.FOE_PREC_BF16, (480, 450)), (F.FOE_PREC_BF16, (40, 50)),
                                         (F.FOE_PREC_TF32, (70, 64)), (F.FOE_PREC_FP32, (33, 47))])
 @pytest.mark.parametrize("every", [10, 7])
 def test_stop_equals_the_fixed_budget_solve_of_that_length(dev, ctx, prec, shape, every):
@@ -147,7 +147,7 @@ def test_budget_before_the_stop_and_tol_zero(dev, ctx):
 
 @pytest.mark.parametrize("graph", [False, True])
 def test_batch_per_image_counts(dev, ctx, graph):
-    shapes = [(128, 128, 300), (64, 90, 300), (40, 33, 300), (130, 70, 30), (96, 200, 300)]
+    shapes = [(450, 460, 300), (64, 90, 300), (40, 33, 300), (130, 70, 30), (96, 200, 300)]
     ys, xs, descs = [], [], []
     for j, (H, W, iters) in enumerate(shapes):
         y = to_dev(synth.poisson_observation(synth.clean_image(H, W, 50 + j), 3.0 + j, 60 + j), dev)
