@@ -154,7 +154,10 @@ foe_status foe_create(const foe_prior *prior, foe_ctx **out)
         (e = cudaMemset(c->d_tol_count, 0, sizeof(unsigned) * foe::kMaxBatch)) ||
         (e = cudaHostAlloc(&c->h_stop, 2 * sizeof(int), cudaHostAllocDefault)) ||
         (e = cudaEventCreateWithFlags(&c->tol_ev[0], cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&c->tol_ev[1], cudaEventDisableTiming)))
+        (e = cudaEventCreateWithFlags(&c->tol_ev[1], cudaEventDisableTiming)) ||
+        (e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming)))
         return fail(e == cudaErrorMemoryAllocation ? FOE_ENOMEM : FOE_ECUDA);
     if (ensure_partials(c, 1024) != FOE_OK) return fail(FOE_ENOMEM);
     *out = c;
@@ -182,6 +185,9 @@ void foe_destroy(foe_ctx *c)
     if (c->h_stop) cudaFreeHost(c->h_stop);
     for (cudaEvent_t e : c->tol_ev)
         if (e) cudaEventDestroy(e);
+    if (c->side_fork) cudaEventDestroy(c->side_fork);
+    if (c->side_join) cudaEventDestroy(c->side_join);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     delete c;
 }

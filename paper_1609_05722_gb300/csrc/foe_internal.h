@@ -45,6 +45,9 @@ struct foe_ctx {
     double *d_tol_part = nullptr;           // [kMaxBatch][kTolBlocks][2]
     unsigned *d_tol_count = nullptr;        // [kMaxBatch], 0 between checks
     int *h_stop = nullptr;                  // pinned [2]
+    // second stream of the tensor-core launches that hold both tile sizes (foe::tc_launch)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaEvent_t tol_ev[2] = {nullptr, nullptr};
     // the last fixed-step solve (foe_iters_done): per image of the call, its budget and its word (-1: none)
     std::vector<int> last_budget, last_word;
@@ -353,7 +356,8 @@ inline foe_status launch(foe_ctx *c, int prec, int mode, cudaStream_t s)
     } else {
         c->args.withhold_arrival = c->withhold_arrival;
         c->withhold_arrival = 0;
-        e = foe::tc_launch(c->args, mode, prec == FOE_PREC_TF32, c->d_status, s);
+        e = foe::tc_launch(c->args, mode, prec == FOE_PREC_TF32, c->d_status, s,
+                           foe::SideStream{c->side_stream, c->side_fork, c->side_join});
         c->args.withhold_arrival = 0;
     }
     if (e != cudaSuccess) {

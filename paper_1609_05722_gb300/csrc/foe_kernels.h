@@ -19,7 +19,13 @@ cudaError_t f32_launch(const LaunchArgs &a, int mode, cudaStream_t s);
 int tc_tile_h(bool tf32, int H, int W);  // output rows of the tensor-core tiles of an H x W image
 int tc_tile_w(int tile_h);        // output columns of those tiles
 cudaError_t tc_setup();
-cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s);
+// A second stream and two events of the caller's context: a launch holding images of both tile sizes runs the
+// 26 x 26 kernel on `stream`, forked from and joined back into the caller's stream, beside the pixel-pair kernel.
+struct SideStream {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s, const SideStream &side);
 int pair_tile();
 int pair_min_rows();
 long pair_min_pixels();

@@ -895,7 +895,7 @@ thread_local PairArgs t_args;
 
 int pair_tile() { return PT; }
 int pair_min_rows() { return kPairMinRows; }
-long pair_min_pixels() { return 200000; }
+long pair_min_pixels() { return 90000; }
 
 cudaError_t pair_setup()
 {

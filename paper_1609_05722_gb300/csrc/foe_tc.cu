@@ -744,10 +744,11 @@ cudaError_t tc_attr()
 
 // BF16 images of at least pair_min_rows() rows and pair_min_pixels() pixels take the pixel-pair kernel's 58 x 58 tiles;
 // the rest take 26 x 26 tiles.  The pair kernel runs one CTA per SM and a tile in about 20 us; the 26 x 26 kernel
-// runs two CTAs per SM and a tile in about 10 us, so it finishes small images sooner (300 iterations: 384^2 alone
-// 3.9 ms against 7.1 ms) while the pair kernel does more per SM once an image fills the GPU (five 512^2 images
-// together: 15.8 ms against 19.5 ms; five 384^2: 11.6 against 11.8 ms).  The choice depends on the image alone, so an
-// image is tiled, and rounded, the same way in any batch.
+// runs two CTAs per SM and a tile in about 10 us, so it finishes small images sooner (300 iterations: 256^2 alone
+// 3.7 ms against 7.1 ms) while the pair kernel does more per SM once there is enough work (five 512^2 images together:
+// 15.8 ms against 19.5 ms).  The threshold of 90000 pixels (300^2) gave the most on 64 uneven images in one batch
+// (29.2 k MPix.iter/s, against 26.6 k at 200000 and 28.9 k with pair tiles for all).  The choice depends on the image
+// alone, so an image is tiled, and rounded, the same way in any batch.
 int tc_tile_h(bool tf32, int H, int W)
 {
     return !tf32 && H >= pair_min_rows() && (long)H * W >= pair_min_pixels() ? pair_tile() : kShortH;
@@ -764,7 +765,7 @@ cudaError_t tc_setup()
     return pair_setup();
 }
 
-cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s)
+cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s, const SideStream &side)
 {
     if (a.nimg <= 0 || a.tile_prefix[a.nimg] <= 0) return cudaSuccess;
     if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
@@ -773,11 +774,19 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     // images tiled 58 x 58 run in the pixel-pair kernel (foe_pair.cu), the others (26 x 26 tiles, and every TF32
-    // image) here; a launch holding both kinds runs as one launch of each kernel
+    // image) here; a launch holding both kinds runs one launch of each kernel at the same time: the 26 x 26 kernel
+    // on the side stream, forked after the work queued so far and joined back before whatever is queued next, so that
+    // each kernel's CTAs take the SMs that the other leaves free (one pair CTA or two 26 x 26 CTAs fit an SM)
     int npair = 0;
     for (int i = 0; i < a.nimg; ++i) npair += a.img[i].tile_h == pair_tile();
+    const bool both = npair > 0 && npair < a.nimg;
+    if (both) {
+        if ((e = cudaEventRecord(side.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
+    }
     if (npair > 0 && (e = pair_launch(a, mode, npair == a.nimg, sms, d_status, s)) != cudaSuccess) return e;
     if (npair == a.nimg) return cudaSuccess;
+    const cudaStream_t s26 = both ? side.stream : s;
     LaunchArgs b = a;
     b.nimg = 0;
     b.tile_prefix[0] = 0;
@@ -790,10 +799,13 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     const int tiles = b.tile_prefix[b.nimg];
     // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
     const int grid = std::min(tiles, 2 * sms);
-    if (tf32) return mode == kStep ? tc_launch_one<kStep, true, kShortH>(b, grid, d_status, s)
-                                   : tc_launch_one<kGrad, true, kShortH>(b, grid, d_status, s);
-    return mode == kStep ? tc_launch_one<kStep, false, kShortH>(b, grid, d_status, s)
-                         : tc_launch_one<kGrad, false, kShortH>(b, grid, d_status, s);
+    if (tf32) e = mode == kStep ? tc_launch_one<kStep, true, kShortH>(b, grid, d_status, s26)
+                                : tc_launch_one<kGrad, true, kShortH>(b, grid, d_status, s26);
+    else e = mode == kStep ? tc_launch_one<kStep, false, kShortH>(b, grid, d_status, s26)
+                           : tc_launch_one<kGrad, false, kShortH>(b, grid, d_status, s26);
+    if (e != cudaSuccess || !both) return e;
+    if ((e = cudaEventRecord(side.join, side.stream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, side.join, 0);
 }
 
 }  // namespace foe

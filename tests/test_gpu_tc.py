@@ -71,7 +71,7 @@ def problem(bank32, H, W, model, bc, tau):
                      gamma=GAMMA)
 
 
-# Images below 200000 pixels or 59 rows (and every TF32 image) take 26 x 26 tiles: widths 54 and 79 leave a last tile
+# Images below 90000 pixels or 59 rows (and every TF32 image) take 26 x 26 tiles: widths 54 and 79 leave a last tile
 # of 2 and 1 columns after full 26-column tiles, where the reflection of a pixel within 3 columns of the right border
 # falls outside a 32-column response region that does not reach it; width 28 puts the flush last tile at column 2,
 # so the columns within 3 of the left border must stay with the first tile.  Larger BF16 images take the 58 x 58
