@@ -121,6 +121,9 @@ typedef struct {
     int H, W, ld;
     float peak;           /* used for FOE_MODEL_AUTO */
     int iters;            /* per-image iteration budget, >= 0 */
+    int use_model;        /* 0: the image takes opts->model; 1: it takes `model` (images of different data
+                             terms then share one batch).  Zero-initialised descriptors keep the first. */
+    foe_model model;      /* read when use_model is 1: DIRECT, ANS_L2, ANS_IDIV or AUTO */
 } foe_image_desc;
 
 /* Fills *opts with the defaults: AUTO model, lambda 1, gamma 0.8, tau 0 (auto), no stopping rule (tol 0,
@@ -213,9 +216,10 @@ FOE_API foe_status foe_denoise_binned(foe_ctx *ctx, const float *y, float *x, in
 FOE_API foe_status foe_denoise_static(foe_ctx *ctx, const float *y, float *x, int H, int W, int ld, float peak,
                                       const foe_solve_opts *opts, void *stream);
 
-/* Denoises n independent images of mixed sizes and iteration budgets in one stream-ordered pass:
+/* Denoises n independent images of mixed sizes, iteration budgets and data terms in one stream-ordered pass:
  * every iteration advances all images whose budget is not yet spent, in one launch over the tiles
- * of all of them.  opts->iters is ignored (each desc carries its own).  With opts->tol > 0 every image has
+ * of all of them.  opts->iters is ignored (each desc carries its own); a desc with use_model = 1 carries its
+ * own model too.  With opts->tol > 0 every image has
  * its own stopping word: the whole budget is queued (nothing is synchronised), and the step launches skip
  * the tiles of images that have stopped, so a launch in which every image has stopped does almost no work. */
 FOE_API foe_status foe_denoise_batch(foe_ctx *ctx, const foe_image_desc *descs, int n, const foe_solve_opts *opts,

@@ -19,7 +19,7 @@ static foe_status enqueue_batch(foe_ctx *c, const foe_image_desc *descs, int n, 
         const size_t plane = (size_t)d.H * d.ld;
         slots[j] = carve(base, plane);
         base += 5 * plane;
-        models[j] = resolve_model(o->model, d.peak);
+        models[j] = resolve_model(d.use_model ? d.model : o->model, d.peak);
         FOE_CUDA(c, foe::launch_init(d.y, d.H, d.W, d.ld, d.ld, models[j], o->zero_c, slots[j].d, slots[j].uh0,
                                      lo_plane(o->prec, slots[j].ul), slots[j].delta, s));
         const float tau = o->tau > 0.0f ? o->tau : default_tau(c->symbol_max, o->bc, o->gamma);
@@ -512,7 +512,10 @@ foe_status foe_denoise_batch(foe_ctx *c, const foe_image_desc *descs, int n, con
         if ((st = check_image(c, d.y, d.H, d.W, d.ld, "desc.y")) != FOE_OK) return st;
         if ((st = check_image(c, d.x, d.H, d.W, d.ld, "desc.x")) != FOE_OK) return st;
         if (d.iters < 0) { set_err(c, "desc.iters must be >= 0"); return FOE_EINVAL; }
-        if (o->model == FOE_MODEL_AUTO && !(d.peak > 0.0f && std::isfinite(d.peak))) {
+        if (d.use_model != 0 && d.use_model != 1) { set_err(c, "desc.use_model must be 0 or 1"); return FOE_EINVAL; }
+        const int m = d.use_model ? d.model : o->model;
+        if (m < FOE_MODEL_DIRECT || m > FOE_MODEL_AUTO) { set_err(c, "desc.model: bad model"); return FOE_EINVAL; }
+        if (m == FOE_MODEL_AUTO && !(d.peak > 0.0f && std::isfinite(d.peak))) {
             set_err(c, "desc.peak must be > 0 for FOE_MODEL_AUTO");
             return FOE_EINVAL;
         }

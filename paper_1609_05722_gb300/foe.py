@@ -43,7 +43,7 @@ class foe_report(C.Structure):
 
 class foe_image_desc(C.Structure):
     _fields_ = [("y", C.c_void_p), ("x", C.c_void_p), ("H", C.c_int), ("W", C.c_int), ("ld", C.c_int),
-                ("peak", C.c_float), ("iters", C.c_int)]
+                ("peak", C.c_float), ("iters", C.c_int), ("use_model", C.c_int), ("model", C.c_int)]
 
 
 class foe_server_config(C.Structure):
@@ -272,10 +272,13 @@ def foe_denoise_static(ctx, y, x, H: int, W: int, ld: int, peak: float, opts: So
 
 
 def foe_denoise_batch(ctx, descs: list[dict], opts: SolveOpts | None = None, stream=None) -> None:
-    """descs: dicts with y, x (device buffers), H, W, ld, peak, iters."""
+    """descs: dicts with y, x (device buffers), H, W, ld, peak, iters, and optionally model (the image's own data
+    term; without it the image takes opts.model)."""
     arr = (foe_image_desc * len(descs))()
     for j, d in enumerate(descs):
-        arr[j] = foe_image_desc(_ptr(d["y"]), _ptr(d["x"]), d["H"], d["W"], d["ld"], d["peak"], d["iters"])
+        m = d.get("model")
+        arr[j] = foe_image_desc(_ptr(d["y"]), _ptr(d["x"]), d["H"], d["W"], d["ld"], d["peak"], d["iters"],
+                                0 if m is None else 1, 0 if m is None else int(m))
     o = (opts or SolveOpts()).c()
     _check(lib().foe_denoise_batch(ctx, arr, len(descs), C.byref(o), _stream(stream)), ctx, "foe_denoise_batch")
 

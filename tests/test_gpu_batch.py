@@ -104,3 +104,28 @@ def test_zero_padding_batch_equals_single_solves(ctx, prec):
         F.foe_denoise(ctx, ys[j], single, s.H, s.W, descs[j]["ld"], s.peak, F.SolveOpts(iters=s.iters, **opts))
         torch.cuda.synchronize()
         assert torch.equal(single[:, :s.W], xs[j][:, :s.W]), j
+
+
+def test_per_image_data_terms_in_one_batch(ctx):
+    # one batch, each image with its own data term (use_model = 1) or the batch's (opts.model): every image equals
+    # its single solve under that model bit for bit; sizes on both sides of the pixel-pair threshold
+    specs = [synth.ImageSpec(512, 512, p, 30, 41 + j, 51 + j) for j, p in enumerate([1.0, 4.0, 8.0])] + \
+            [synth.ImageSpec(160, 200, p, 30, 61 + j, 71 + j) for j, p in enumerate([2.0, 30.0, 6.0])]
+    models = [F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2, None, F.FOE_MODEL_ANS_IDIV, F.FOE_MODEL_AUTO, None]
+    ys, xs, descs = upload(specs)
+    for d, m in zip(descs, models):
+        if m is not None:
+            d["model"] = m
+    F.foe_denoise_batch(ctx, descs, F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_BF16))
+    torch.cuda.synchronize()
+    for j, (s, m) in enumerate(zip(specs, models)):
+        single = torch.zeros_like(xs[j])
+        F.foe_denoise(ctx, ys[j], single, s.H, s.W, descs[j]["ld"], s.peak,
+                      F.SolveOpts(model=F.FOE_MODEL_ANS_L2 if m is None else m, iters=s.iters, prec=F.FOE_PREC_BF16))
+        torch.cuda.synchronize()
+        assert torch.equal(single[:, :s.W], xs[j][:, :s.W]), j
+    # a model outside the enumeration is refused
+    bad = [dict(descs[0], model=7)]
+    with pytest.raises(F.FoeError) as e:
+        F.foe_denoise_batch(ctx, bad, F.SolveOpts())
+    assert e.value.status == F.FOE_EINVAL
