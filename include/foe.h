@@ -167,8 +167,11 @@ FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted
  * L uses tau = 2 (1 - gamma) / (L + 2e-3) and is accepted when
  *   F(u+) <= F(u) + <grad F(u), u+ - u> + L/2 ||u+ - u||^2    (FP64 reductions on the GPU),
  * otherwise L doubles and the step is retried from the same u; after each accepted step L is divided by 1.5.
- * L starts at the bound of foe_step_size (or at the L implied by opts.tau when it is > 0).  The host reads
- * three scalars per trial (one synchronisation each), so this mode is for accuracy, not throughput.
+ * L starts at the bound of foe_step_size (or at the L implied by opts.tau when it is > 0).  Every decision is
+ * taken on the device: an iteration is one CUDA graph launch (gradient, snapshot, then a conditional loop of
+ * trials that a one-thread kernel ends by accepting), all iterations are queued without waiting, and the host
+ * synchronises once at the end.  A trial costs a step, an energy evaluation and two reductions, so this mode is
+ * for accuracy, not throughput.
  * foe_step_log returns the trials of the last such solve.
  * With opts.tol > 0 (fixed steps) the host reads the image's stopping word one check interval behind the
  * device (an event on the stream; the next interval is queued meanwhile), issues no launch past the interval

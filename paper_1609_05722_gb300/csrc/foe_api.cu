@@ -180,6 +180,9 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->ws);
     cudaFree(c->d_bin);
     cudaFree(c->d_stop);
+    cudaFree(c->d_bt);
+    cudaFree(c->d_bt_tau);
+    cudaFree(c->d_bt_acc);
     cudaFree(c->d_tol_part);
     cudaFree(c->d_tol_count);
     if (c->h_stop) cudaFreeHost(c->h_stop);
@@ -206,6 +209,24 @@ foe_status foe_step_size(const foe_ctx *ctx, foe_bc bc, float gamma, float *tau_
 // the host); otherwise L doubles and the trial is repeated from the same u.  After an accepted step L is divided
 // by 1.5.  L starts at the context's certified bound (or at the L implied by opts->tau when it is set).  Every
 // trial is one fused FP32 step launch, so rejected trials restore u_lo and delta from a snapshot.
+// Owns the graphs of a backtracking solve (destroyed on every return path).
+struct BtGraphs {
+    cudaGraph_t g[2] = {nullptr, nullptr};
+    cudaGraphExec_t x[2] = {nullptr, nullptr};
+    ~BtGraphs()
+    {
+        for (int i = 0; i < 2; ++i) {
+            if (x[i]) cudaGraphExecDestroy(x[i]);
+            if (g[i]) cudaGraphDestroy(g[i]);
+        }
+    }
+};
+
+// FOE_STEP_BACKTRACK (FP32): every accept / reject decision is taken on the device.  An iteration is one launch of
+// a CUDA graph: the prior gradient at u^n and a snapshot of u_lo and delta, then a conditional WHILE node whose body
+// is one trial (restore the snapshot, the step with the trial's constants read from device memory, the FP64
+// reductions, F(u+), k_bt_decide, which sets the loop condition).  Two graphs alternate the iterate planes.  The
+// host queues all iterations without waiting and reads the state and the trial log once at the end.
 static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H, int W, int ld, int model,
                                     const foe_solve_opts *o, cudaStream_t s, foe_report *rep)
 {
@@ -219,9 +240,10 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
     Slot sl = carve((float *)c->ws, plane);
     float *gpl = (float *)c->ws + 5 * plane, *snap_lo = gpl + plane, *snap_dl = snap_lo + plane;
     const double c2 = 1e-3, gam = o->gamma;
+    const bool tol_on = o->tol > 0.0f;
     int tiles = 0;
     // launch arguments for one image: read u0 (parity 0), write u1; prior_only for the gradient / energy
-    auto set_args = [&](float *u0, float *u1, float tau, int prior_only) {
+    auto set_args = [&](float *u0, float *u1, int prior_only) {
         args_begin(c, o->bc);
         ImgDesc d{};
         d.u_hi[0] = u0;
@@ -234,101 +256,150 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         d.W = W;
         d.ld = ld;
         d.model = model;
-        d.sc = step_consts(tau, o->gamma, o->lambda);
+        d.sc = step_consts(0.0f, o->gamma, o->lambda);  // the step launches read the trial's constants on the device
+        d.stop = tol_on ? c->d_stop : nullptr;
         args_add(c, FOE_PREC_FP32, d);
         c->args.prior_only = prior_only;
         tiles = c->args.tile_prefix[1];
     };
-    set_args(sl.uh0, nullptr, 0.0f, 1);
+    set_args(sl.uh0, nullptr, 1);
     const int nb = foe::dot2_blocks(H);
     if ((st = ensure_partials(c, tiles + 2 * nb + 4)) != FOE_OK) return st;
     double *dot_part = c->d_partials + tiles, *outs = dot_part + 2 * nb;  // outs: <g, du>, |du|^2, F(u+)
-    auto prior_energy = [&](float *u, double *dst) -> foe_status {
-        set_args(u, nullptr, 0.0f, 1);
+    const int cap = std::max(1, std::min(o->iters * 61, 1 << 20));     // trial log entries kept
+    if ((st = ensure_bt(c, cap)) != FOE_OK) return st;
+    auto prior_energy = [&](float *u, double *dst, cudaStream_t q) -> foe_status {
+        set_args(u, nullptr, 1);
         c->args.partials = c->d_partials;
-        foe_status e = launch(c, FOE_PREC_FP32, foe::kEnergy, s);
+        foe_status e = launch(c, FOE_PREC_FP32, foe::kEnergy, q);
         if (e != FOE_OK) return e;
-        FOE_CUDA(c, foe::launch_reduce(c->d_partials, tiles, dst, s));
+        FOE_CUDA(c, foe::launch_reduce(c->d_partials, tiles, dst, q));
         return FOE_OK;
     };
 
     FOE_CUDA(c, foe::launch_init(y, H, W, ld, ld, model, o->zero_c, sl.d, sl.uh0, sl.ul, sl.delta, s));
-    double L = o->tau > 0.0f ? 2.0 * (1.0 - gam) / (double)o->tau - 2.0 * c2 : 2.0 * kappa(o->bc) * c->symbol_max;
-    if (!(L > 0.0)) {
+    const double L0 = o->tau > 0.0f ? 2.0 * (1.0 - gam) / (double)o->tau - 2.0 * c2 : 2.0 * kappa(o->bc) * c->symbol_max;
+    if (!(L0 > 0.0)) {
         set_err(c, "opts->tau implies a non-positive Lipschitz estimate");
         return FOE_EINVAL;
     }
-    c->bt_tau.clear();
-    c->bt_accepted.clear();
-    const bool tol_on = o->tol > 0.0f;
     if (tol_on) FOE_CUDA(c, cudaMemsetAsync(c->d_stop, 0, sizeof(int), s));
-    int done = o->iters;
-    double h[3], Fn = 0.0;
-    if ((st = prior_energy(sl.uh0, outs + 2)) != FOE_OK) return st;
-    FOE_CUDA(c, cudaMemcpyAsync(&Fn, outs + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    FOE_CUDA(c, cudaStreamSynchronize(s));
-    float *cur = sl.uh0, *nxt = sl.uh1;
-    int backtracks = 0;
-    float tau = 0.0f;
-    for (int n = 0; n < o->iters; ++n) {
-        set_args(cur, nullptr, 0.0f, 1);
-        if ((st = launch(c, FOE_PREC_FP32, foe::kGrad, s)) != FOE_OK) return st;  // g = grad F(u^n)
-        FOE_CUDA(c, cudaMemcpyAsync(snap_lo, sl.ul, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        FOE_CUDA(c, cudaMemcpyAsync(snap_dl, sl.delta, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        for (int trial = 0;; ++trial) {
-            if (trial > 0) {
-                FOE_CUDA(c, cudaMemcpyAsync(sl.ul, snap_lo, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
-                FOE_CUDA(c, cudaMemcpyAsync(sl.delta, snap_dl, plane * sizeof(float), cudaMemcpyDeviceToDevice, s));
-            }
-            tau = (float)(2.0 * (1.0 - gam) / (L + 2.0 * c2));
-            set_args(cur, nxt, tau, 0);
-            if ((st = launch(c, FOE_PREC_FP32, foe::kStep, s)) != FOE_OK) return st;  // u+ (delta = u+ - u^n)
-            FOE_CUDA(c, foe::launch_dot2(gpl, sl.delta, H, W, ld, dot_part, outs, s));
-            if ((st = prior_energy(nxt, outs + 2)) != FOE_OK) return st;
-            FOE_CUDA(c, cudaMemcpyAsync(h, outs, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            FOE_CUDA(c, cudaStreamSynchronize(s));
-            if (!std::isfinite(h[0]) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
-                set_err(c, "non-finite energy or step at iteration %d", n);
-                return FOE_ENONFINITE;
-            }
-            const bool accept = h[2] <= Fn + h[0] + 0.5 * L * h[1];
-            c->bt_tau.push_back(tau);
-            c->bt_accepted.push_back(accept ? 1 : 0);
-            if (accept) {
-                Fn = h[2];
-                break;
-            }
-            L *= 2.0;
-            ++backtracks;
-            if (trial >= 60) {
-                set_err(c, "backtracking did not find an accepted step at iteration %d", n);
-                return FOE_ENONFINITE;
-            }
+    if ((st = prior_energy(sl.uh0, outs + 2, s)) != FOE_OK) return st;
+    FOE_CUDA(c, foe::launch_bt_init(c->d_bt, outs + 2, L0, gam, 2.0 * c2, o->gamma, o->lambda, cap, s));
+
+    // the two iteration graphs, captured on the context's side stream (capture only: they run on s)
+    BtGraphs G;
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    FOE_CUDA(c, cudaStreamIsCapturing(c->side_stream, &cap_status));
+    if (cap_status != cudaStreamCaptureStatusNone) {
+        set_err(c, "FOE_STEP_BACKTRACK: the context's side stream is being captured");
+        return FOE_EINVAL;
+    }
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    for (int par = 0; par < 2; ++par) {
+        float *cur = par ? sl.uh1 : sl.uh0, *nxt = par ? sl.uh0 : sl.uh1;
+        FOE_CUDA(c, cudaGraphCreate(&G.g[par], 0));
+        // gradient at u^n and the snapshot
+        FOE_CUDA(c, cudaStreamBeginCaptureToGraph(c->side_stream, G.g[par], nullptr, nullptr, 0, mode));
+        set_args(cur, nullptr, 1);
+        st = launch(c, FOE_PREC_FP32, foe::kGrad, c->side_stream);
+        cudaError_t ce = cudaSuccess;
+        if (st == FOE_OK) ce = cudaMemcpyAsync(snap_lo, sl.ul, plane * sizeof(float), cudaMemcpyDeviceToDevice, c->side_stream);
+        if (st == FOE_OK && ce == cudaSuccess)
+            ce = cudaMemcpyAsync(snap_dl, sl.delta, plane * sizeof(float), cudaMemcpyDeviceToDevice, c->side_stream);
+        cudaGraph_t got = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->side_stream, &got);
+        if (st != FOE_OK) return st;
+        FOE_CUDA(c, ce);
+        FOE_CUDA(c, ee);
+        size_t npre = 0;
+        FOE_CUDA(c, cudaGraphGetNodes(G.g[par], nullptr, &npre));
+        std::vector<cudaGraphNode_t> pre(npre);
+        FOE_CUDA(c, cudaGraphGetNodes(G.g[par], pre.data(), &npre));
+        // the trial loop
+        cudaGraphConditionalHandle h;
+        FOE_CUDA(c, cudaGraphConditionalHandleCreate(&h, G.g[par], 1u, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        FOE_CUDA(c, cudaGraphAddNode(&loop, G.g[par], pre.data(), nullptr, npre, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        FOE_CUDA(c, cudaStreamBeginCaptureToGraph(c->side_stream, body, nullptr, nullptr, 0, mode));
+        ce = cudaMemcpyAsync(sl.ul, snap_lo, plane * sizeof(float), cudaMemcpyDeviceToDevice, c->side_stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(sl.delta, snap_dl, plane * sizeof(float), cudaMemcpyDeviceToDevice, c->side_stream);
+        if (ce == cudaSuccess) {
+            set_args(cur, nxt, 0);
+            c->args.sc_dev = &c->d_bt->sc;
+            st = launch(c, FOE_PREC_FP32, foe::kStep, c->side_stream);  // u+ (delta = u+ - u^n)
+            c->args.sc_dev = nullptr;
         }
-        std::swap(cur, nxt);
-        L /= 1.5;
+        if (ce == cudaSuccess && st == FOE_OK) ce = foe::launch_dot2(gpl, sl.delta, H, W, ld, dot_part, outs, c->side_stream);
+        if (ce == cudaSuccess && st == FOE_OK) st = prior_energy(nxt, outs + 2, c->side_stream);
+        if (ce == cudaSuccess && st == FOE_OK)
+            ce = foe::launch_bt_decide(h, c->d_bt, outs, c->d_bt_tau, c->d_bt_acc, tol_on ? c->d_stop : nullptr,
+                                       c->side_stream);
+        got = nullptr;
+        const cudaError_t eb = cudaStreamEndCapture(c->side_stream, &got);
+        if (st != FOE_OK) return st;
+        FOE_CUDA(c, ce);
+        FOE_CUDA(c, eb);
+        FOE_CUDA(c, cudaGraphInstantiate(&G.x[par], G.g[par], 0));
+    }
+
+    // the iterations: queued without waiting; the stopping rule is checked between them
+    ImgDesc td{};
+    td.u_hi[0] = sl.uh0;
+    td.u_hi[1] = sl.uh1;
+    td.u_lo = sl.ul;
+    td.delta = sl.delta;
+    td.H = H;
+    td.W = W;
+    td.ld = ld;
+    td.stop = c->d_stop;
+    for (int n = 0; n < o->iters; ++n) {
+        FOE_CUDA(c, cudaGraphLaunch(G.x[n & 1], s));
         if (tol_on && (n + 1) % o->tol_every == 0) {
-            // the host waits on every trial here anyway: check u^{n+1} and read the word at once
             foe::TolArgs t;
             t.nimg = 1;
             t.n = n + 1;
             t.tol = (double)o->tol;
             t.partials = c->d_tol_part;
             t.count = c->d_tol_count;
-            t.img[0] = foe::TolImg{cur, sl.ul, sl.delta, H, W, ld, c->d_stop};
+            t.img[0] = tol_img(td, n + 1);
             FOE_CUDA(c, foe::launch_tol_check(t, s));
-            FOE_CUDA(c, cudaMemcpyAsync(c->h_stop, c->d_stop, sizeof(int), cudaMemcpyDeviceToHost, s));
-            FOE_CUDA(c, cudaStreamSynchronize(s));
-            if (c->h_stop[0] != 0) {
-                done = n + 1;
-                break;
-            }
         }
     }
+    foe::BtState bs{};
+    int stop = 0;
+    FOE_CUDA(c, cudaMemcpyAsync(&bs, c->d_bt, sizeof(bs), cudaMemcpyDeviceToHost, s));
+    if (tol_on) FOE_CUDA(c, cudaMemcpyAsync(&stop, c->d_stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FOE_CUDA(c, cudaStreamSynchronize(s));
+    const int nlog = std::min(bs.nlog, cap);
+    c->bt_tau.resize(nlog);
+    c->bt_accepted.resize(nlog);
+    if (nlog > 0) {
+        FOE_CUDA(c, cudaMemcpy(c->bt_tau.data(), c->d_bt_tau, sizeof(float) * nlog, cudaMemcpyDeviceToHost));
+        FOE_CUDA(c, cudaMemcpy(c->bt_accepted.data(), c->d_bt_acc, nlog, cudaMemcpyDeviceToHost));
+    }
+    if (bs.status == foe::kBtNonFinite) {
+        set_err(c, "non-finite energy or step during backtracking");
+        return FOE_ENONFINITE;
+    }
+    if (bs.status == foe::kBtNoStep) {
+        set_err(c, "backtracking did not find an accepted step within 61 trials");
+        return FOE_ENONFINITE;
+    }
+    const int done = stop ? stop : o->iters;
     const int word = tol_on ? 0 : -1;
     note_solve(c, 1, &o->iters, &word);
+    const float *uf = (o->iters & 1) ? sl.uh1 : sl.uh0, *ua = (o->iters & 1) ? sl.uh0 : sl.uh1;
     if (rep) FOE_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), s));
-    FOE_CUDA(c, foe::launch_output(cur, sl.ul, H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s));
+    FOE_CUDA(c, foe::launch_output(uf, sl.ul, H, W, ld, ld, model, x, rep ? c->d_nonfinite : nullptr, s, nullptr, ua,
+                                   o->iters, tol_on ? c->d_stop : nullptr));
     if (rep) {
         int dev_status = 0, nonfinite = 0;
         FOE_CUDA(c, cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -337,10 +408,10 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         rep->nonfinite = nonfinite;
         rep->iters_done = done;
         rep->model_used = model;
-        rep->tau_used = tau;
+        rep->tau_used = bs.tau_last;
         rep->status = dev_status ? (foe_status)dev_status : FOE_OK;
-        rep->backtracks = backtracks;
-        rep->lipschitz_final = L;
+        rep->backtracks = bs.rejected;
+        rep->lipschitz_final = bs.L;
         if (nonfinite) {
             set_err(c, "%d non-finite output pixels", nonfinite);
             return FOE_ENONFINITE;

@@ -63,7 +63,84 @@ __global__ void k_dot2_final(const double *partials, int n, double *out)
     }
 }
 
+// tau and the step constants of trial L (the same expressions as the host used, evaluated in IEEE double)
+__device__ __forceinline__ void bt_set_trial(BtState *st)
+{
+    st->tau = (float)(2.0 * (1.0 - st->gam) / (st->L + st->c2));
+    st->sc = make_step_consts(st->tau, st->gamma, st->lambda);
+}
+
+__global__ void k_bt_init(BtState *st, const double *F0, double L0, double gam, double c2, float gamma, float lambda,
+                          int cap)
+{
+    st->L = L0;
+    st->Fn = *F0;
+    st->gam = gam;
+    st->c2 = c2;
+    st->gamma = gamma;
+    st->lambda = lambda;
+    st->trial = st->rejected = st->nlog = st->status = 0;
+    st->cap = cap;
+    st->tau_last = 0.0f;
+    bt_set_trial(st);
+}
+
+__global__ void k_bt_decide(cudaGraphConditionalHandle h, BtState *st, const double *outs, float *log_tau,
+                            unsigned char *log_acc, const int *stop)
+{
+    // a stopped image (stopping rule) or a failed solve: leave the state as it is and end the trial loop
+    if (st->status != 0 || (stop && *(const volatile int *)stop != 0)) {
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const double g_du = outs[0], du2 = outs[1], F1 = outs[2];
+    if (!isfinite(g_du) || !isfinite(du2) || !isfinite(F1)) {
+        st->status = kBtNonFinite;
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const bool accept = F1 <= fma(0.5 * st->L, du2, st->Fn + g_du);
+    if (st->nlog < st->cap) {
+        log_tau[st->nlog] = st->tau;
+        log_acc[st->nlog] = accept ? 1 : 0;
+    }
+    st->nlog++;
+    if (accept) {
+        st->Fn = F1;
+        st->tau_last = st->tau;
+        st->L /= 1.5;
+        st->trial = 0;
+        bt_set_trial(st);
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    st->L *= 2.0;
+    st->rejected++;
+    if (st->trial >= 60) {
+        st->status = kBtNoStep;
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    st->trial++;
+    bt_set_trial(st);
+    cudaGraphSetConditional(h, 1u);
+}
+
 }  // namespace
+
+cudaError_t launch_bt_init(BtState *st, const double *F0, double L0, double gam, double c2, float gamma, float lambda,
+                           int cap, cudaStream_t s)
+{
+    k_bt_init<<<1, 1, 0, s>>>(st, F0, L0, gam, c2, gamma, lambda, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bt_decide(cudaGraphConditionalHandle h, BtState *st, const double *outs, float *log_tau,
+                             unsigned char *log_acc, const int *stop, cudaStream_t s)
+{
+    k_bt_decide<<<1, 1, 0, s>>>(h, st, outs, log_tau, log_acc, stop);
+    return cudaGetLastError();
+}
 
 int dot2_blocks(int H) { return (H + kRowsPerBlock - 1) / kRowsPerBlock; }
 

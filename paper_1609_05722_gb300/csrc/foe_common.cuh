@@ -27,6 +27,25 @@ struct StepConsts {
     float a2_hi, a2_lo;        // c / (1 + c)
 };
 
+// The constants of a step of size tau (host and device: the backtracking decides tau on the device and must
+// reproduce the host's constants exactly, so no FMA contraction applies here: only products, sums and quotients).
+__host__ __device__ inline StepConsts make_step_consts(float tau, float gamma, float lambda)
+{
+    StepConsts s;
+    s.tau = tau;
+    s.gamma = gamma;
+    s.lambda = lambda;
+    const double c = (double)tau * (double)lambda;  // exact: a product of two floats
+    const double d = 1.0 + c;
+    const double v[3] = {c, 1.0 / d, c / d};
+    float *hi[3] = {&s.c_hi, &s.a1_hi, &s.a2_hi}, *lo[3] = {&s.c_lo, &s.a1_lo, &s.a2_lo};
+    for (int i = 0; i < 3; ++i) {
+        *hi[i] = (float)v[i];
+        *lo[i] = (float)(v[i] - (double)*hi[i]);
+    }
+    return s;
+}
+
 // One image of a launch.  u_hi is double-buffered: a launch reads u_hi[parity] (with halos) and
 // writes u_hi[parity ^ 1]; u_lo and delta are private to each pixel and updated in place.
 struct ImgDesc {
@@ -58,6 +77,8 @@ struct LaunchArgs {
     const void *tcops;         // tensor-core operand images (bf16): forward filters, then adjoint filters
     const void *tcops32;       // the same images in tf32
     const void *pairops;       // operand images of the pixel-pair kernel (bf16)
+    const StepConsts *sc_dev;  // nullable: the step constants of every image of a kStep launch of the FP32 kernel,
+                               // read from device memory (backtracking decides the step on the device)
     int tile_prefix[kMaxBatch + 1];
     ImgDesc img[kMaxBatch];
 };

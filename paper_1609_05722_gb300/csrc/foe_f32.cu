@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
         } else {
             const float ul = D.u_lo ? D.u_lo[idx] : 0.0f;
             float nh, nl, nd;
-            ipiano_update(g, uh, ul, D.delta[idx], D.d[idx], D.model, D.sc, nh, nl, nd);
+            ipiano_update(g, uh, ul, D.delta[idx], D.d[idx], D.model, A.sc_dev ? *A.sc_dev : D.sc, nh, nl, nd);
             D.u_hi[A.parity ^ 1][idx] = nh;
             if (D.u_lo) D.u_lo[idx] = nl;
             D.delta[idx] = nd;

@@ -58,9 +58,13 @@ struct foe_ctx {
     cudaGraphExec_t batch_exec = nullptr;   // cached graph of the last captured foe_denoise_batch
     long prof_launches = 0;
     double prof_pixel_iters = 0.0;
-    // trial log of the last FOE_STEP_BACKTRACK solve (foe_step_log)
+    // trial log of the last FOE_STEP_BACKTRACK solve (foe_step_log), and its device-side state and log
     std::vector<float> bt_tau;
     std::vector<unsigned char> bt_accepted;
+    foe::BtState *d_bt = nullptr;
+    float *d_bt_tau = nullptr;
+    unsigned char *d_bt_acc = nullptr;
+    int bt_cap = 0;
     char err[512] = {};
 };
 
@@ -289,22 +293,7 @@ inline foe_status check_image(foe_ctx *c, const void *p, int H, int W, int ld, c
 
 inline int resolve_model(int model, float peak) { return model == FOE_MODEL_AUTO ? (peak >= 5.0f ? foe::kAnsL2 : foe::kAnsIdiv) : model; }
 
-inline foe::StepConsts step_consts(float tau, float gamma, float lambda)
-{
-    foe::StepConsts s;
-    s.tau = tau;
-    s.gamma = gamma;
-    s.lambda = lambda;
-    const double c = (double)tau * (double)lambda;
-    auto split = [](double v, float &hi, float &lo) {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
-    };
-    split(c, s.c_hi, s.c_lo);
-    split(1.0 / (1.0 + c), s.a1_hi, s.a1_lo);
-    split(c / (1.0 + c), s.a2_hi, s.a2_lo);
-    return s;
-}
+inline foe::StepConsts step_consts(float tau, float gamma, float lambda) { return foe::make_step_consts(tau, gamma, lambda); }
 
 inline void tile_dims(int prec, int H, int W, int &th, int &tw)
 {
@@ -331,6 +320,7 @@ inline void args_begin(foe_ctx *c, int bc)
     A.tcops = c->d_tcops;
     A.tcops32 = c->d_tcops32;
     A.pairops = c->d_pairops;
+    A.sc_dev = nullptr;
     A.tile_prefix[0] = 0;
 }
 
@@ -386,6 +376,22 @@ inline foe_status ensure_bin(foe_ctx *c, size_t bytes)
     c->bin_bytes = 0;
     FOE_CUDA(c, cudaMalloc(&c->d_bin, bytes));
     c->bin_bytes = bytes;
+    return FOE_OK;
+}
+
+// Device state and a trial log of `cap` entries for FOE_STEP_BACKTRACK.
+inline foe_status ensure_bt(foe_ctx *c, int cap)
+{
+    if (!c->d_bt) FOE_CUDA(c, cudaMalloc(&c->d_bt, sizeof(foe::BtState)));
+    if (cap <= c->bt_cap) return FOE_OK;
+    if (c->d_bt_tau) FOE_CUDA(c, cudaFree(c->d_bt_tau));
+    if (c->d_bt_acc) FOE_CUDA(c, cudaFree(c->d_bt_acc));
+    c->d_bt_tau = nullptr;
+    c->d_bt_acc = nullptr;
+    c->bt_cap = 0;
+    FOE_CUDA(c, cudaMalloc(&c->d_bt_tau, sizeof(float) * (size_t)cap));
+    FOE_CUDA(c, cudaMalloc(&c->d_bt_acc, (size_t)cap));
+    c->bt_cap = cap;
     return FOE_OK;
 }
 

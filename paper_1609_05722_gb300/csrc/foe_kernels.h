@@ -99,6 +99,28 @@ cudaError_t launch_upscale3(const float *xb, int ldb, float *x, int H, int W, in
 // Step control (foe_backtrack.cu): out[0] = sum g * dl, out[1] = sum dl * dl over an H x W plane (pitch ld),
 // FP64, in a fixed order (per-block partials in `partials`, 2 * dot2_blocks(H) doubles, then one block).
 int dot2_blocks(int H);
+
+// Device-side step decision (foe_backtrack.cu).  One trial of iteration n: the step with the trial's constants
+// (st->sc), the two reductions above and F(u+); then k_bt_decide accepts it when
+//   F(u+) <= F(u^n) + <grad F(u^n), u+ - u^n> + L/2 ||u+ - u^n||^2   (FP64, right side as fma(L/2, |du|^2, F + <g,du>))
+// and sets the loop condition of the trial loop (a CUDA graph conditional node): 0 when accepted (L / 1.5 for the
+// next iteration), 1 to retry with 2 L; more than 60 rejections in one iteration, or a non-finite scalar, end the
+// solve with st->status set.
+constexpr int kBtNoStep = 1, kBtNonFinite = 2;
+struct BtState {
+    double L, Fn;              // current estimate, F(u^n)
+    double gam, c2;            // gamma (as a double), the 2 c2 term of tau = 2 (1 - gamma) / (L + 2 c2)
+    float gamma, lambda;       // as the step constants take them
+    float tau, tau_last;       // the current trial's step, the last accepted one
+    int trial, rejected;       // trial index within the iteration, rejected trials so far
+    int nlog, cap;             // trial log entries written (counting those past the capacity), capacity
+    int status;                // 0, kBtNoStep, kBtNonFinite
+    StepConsts sc;             // constants of the current trial
+};
+cudaError_t launch_bt_init(BtState *st, const double *F0, double L0, double gam, double c2, float gamma, float lambda,
+                           int cap, cudaStream_t s);
+cudaError_t launch_bt_decide(cudaGraphConditionalHandle h, BtState *st, const double *outs, float *log_tau,
+                             unsigned char *log_acc, const int *stop, cudaStream_t s);
 cudaError_t launch_dot2(const float *g, const float *dl, int H, int W, int ld, double *partials, double *out,
                         cudaStream_t s);
 
