@@ -736,6 +736,20 @@ def main():
         train["implicit"] = {"ms_per_step": e0.elapsed_time(e1), "cg_iters": irep["cg_iters"],
                              "cg_relres": irep["cg_relres"], "breakdowns": irep["breakdowns"],
                              "grad_norm": float(torch.linalg.vector_norm(dki))}
+        # the same with the CG's Hessian-vector products on TF32 tensor cores
+        dkt = torch.zeros_like(dkg)
+        dat = torch.zeros_like(dag)
+        topts_tc = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_TF32, iters=TT)
+        F.foe_train_grad_implicit(ctx, cl, nz, TB, TH, TW, tld, topts_tc, dkt, dat, 200, 1e-5, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, trep = F.foe_train_grad_implicit(ctx, cl, nz, TB, TH, TW, tld, topts_tc, dkt, dat, 200, 1e-5, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        train["implicit_tf32_hvp"] = {
+            "ms_per_step": e0.elapsed_time(e1), "cg_iters": trep["cg_iters"], "cg_relres": trep["cg_relres"],
+            "grad_rel_diff_vs_fp32": float(torch.linalg.vector_norm(dkt - dki) / torch.linalg.vector_norm(dki))}
         del cl, nz
 
     # serving leg: continuous batching under a 40 GB budget vs the plain per-request paths

@@ -278,7 +278,13 @@ typedef struct {
  * are the parameters (the basis of Eq. filtercoe is the identity).  Unlike foe_train_step this needs no stored
  * iterates: memory is 10 planes per image whatever T is.  It equals the unrolled gradient as T grows (when the
  * iteration converges) and is exact only at a minimiser.
- *   clean, noisy, opts, loss_host, dfilters, dlogalpha  as foe_train_step
+ *   clean, noisy, opts, loss_host, dfilters, dlogalpha  as foe_train_step, except that opts->prec may also be
+ *       FOE_PREC_TF32: the Hessian-vector products of the CG then run on the tensor cores (TF32 operands, FP32
+ *       accumulation; the factors rho''(K_i w*) / 2 are computed once, 48 floats per pixel, 192 B per pixel and
+ *       image of context memory), the lower-level solve and the final gradients stay FP32.  The CG then solves
+ *       with the TF32 operator, whose products differ from the FP32 ones at TF32 rounding level (~5e-4), so the
+ *       CG's residual is that of the TF32 operator; the gradients stay within 1e-3 of the FP32 route's (2e-4
+ *       measured against the FP64 oracle).
  *   max_cg >= 1, cg_tol >= 0 (0: run max_cg iterations)
  *   rep      host, nullable: CG iterations and residuals (synchronises the stream) */
 FOE_API foe_status foe_train_grad_implicit(foe_ctx *ctx, const float *clean, const float *noisy, int B, int H, int W,

@@ -183,6 +183,7 @@ void foe_destroy(foe_ctx *c)
     cudaFree(c->d_bt);
     cudaFree(c->d_bt_tau);
     cudaFree(c->d_bt_acc);
+    cudaFree(c->d_hess);
     cudaFree(c->d_tol_part);
     cudaFree(c->d_tol_count);
     if (c->h_stop) cudaFreeHost(c->h_stop);

@@ -15,7 +15,8 @@ constexpr int kMaxBatch = 64;
 
 enum Model : int { kDirect = 0, kAnsL2 = 1, kAnsIdiv = 2 };
 enum Bc : int { kSymmetric = 0, kZero = 1 };
-enum Mode : int { kStep = 0, kGrad = 1, kEnergy = 2 };
+// kHess / kHvp (tensor-core kernel, TF32): the Hessian factors of the responses of u, then Hessian-vector products
+enum Mode : int { kStep = 0, kGrad = 1, kEnergy = 2, kHvp = 3, kHess = 4 };
 
 // Constants of one iPiano step (Eq. iPianoupdate) for one image.  Products that must stay
 // accurate (tau*lambda and the quadratic prox weights) are carried as FP32 pairs hi + lo,
@@ -59,6 +60,9 @@ struct ImgDesc {
     int tile_h;                // tensor-core path: output rows of this image's tiles
     int model;
     StepConsts sc;
+    float *hess;               // kHess writes, kHvp reads: per pixel the 48 factors (1 - r^2) / (1 + r^2)^2 of the
+                               // responses r of u (the curvature rho'' / 2 of Sec. 2.5.2), [H][W][48] in the order
+                               // of the tensor-core kernel's response columns
     const int *stop;           // nullable: the image's stopping word; non-zero once its stopping rule has held (the
                                // step count at that check), after which every step launch leaves the image as it is
 };

@@ -65,6 +65,9 @@ struct foe_ctx {
     float *d_bt_tau = nullptr;
     unsigned char *d_bt_acc = nullptr;
     int bt_cap = 0;
+    // Hessian factors of foe_train_grad_implicit's tensor-core Hessian-vector products ([B][H][W][48] floats)
+    float *d_hess = nullptr;
+    size_t hess_bytes = 0;
     char err[512] = {};
 };
 

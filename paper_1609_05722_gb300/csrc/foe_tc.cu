@@ -349,15 +349,17 @@ __device__ __forceinline__ void stage_operands(const LaunchArgs &A, TcSmem<TF, T
             if (gy >= H || gx >= W) continue;
             const size_t idx = (size_t)gy * ld + gx;
             if (MODE == kStep) cp_async4(&S.O[0][j], D.delta + idx);
-            cp_async4(&S.O[1][j], D.d + idx);
+            if (MODE == kStep || MODE == kGrad) cp_async4(&S.O[1][j], D.d + idx);
         }
     }
 }
 
 // Persistent: CTA c processes tiles c, c + gridDim.x, ...; tensor memory, barriers and the filter operands
 // are set up once, and the input region of the next tile is copied in while the current one is computed.
+// (kHvp / kHess hold 48 Hessian factors per expert thread: one CTA per SM, which leaves them the registers)
 template <int MODE, bool TF, int TOH>
-__global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
+__global__ void __launch_bounds__(NTHR, (MODE == kHvp || MODE == kHess) ? 1 : 2)
+    k_foe_tc(const __grid_constant__ LaunchArgs A, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem<TF, TOH> &S = *reinterpret_cast<TcSmem<TF, TOH> *>(smem_raw);
@@ -533,11 +535,29 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 bool done = false;
                 for (int t = 0; t < kNMT<TOH>; ++t) {
                     const int g = kNMT<TOH> * k + t;
+                    const int gy = oy0 - 3 + 4 * t + q;
+                    const bool in_img = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                    const uint32_t keep = (interior || in_img) ? 0xFFFFFFFFu : 0u;
+                    // kHvp: the Hessian factors of this lane's response pixel, loaded before the wait so that the
+                    // load overlaps it (zero outside the image, where the product is masked anyway)
+                    float fh[MODE == kHvp ? 48 : 1];
+                    if constexpr (MODE == kHvp) {
+                        const float4 *fp = reinterpret_cast<const float4 *>(D.hess + ((size_t)gy * W + gx) * 48);
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) {
+                            const float4 v = in_img ? __ldg(fp + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            fh[4 * j] = v.x;
+                            fh[4 * j + 1] = v.y;
+                            fh[4 * j + 2] = v.z;
+                            fh[4 * j + 3] = v.w;
+                        }
+                    }
+                    // kHess: the factors are stored for the pixels of the tile's own output region (every image pixel
+                    // belongs to one tile), so each is written once
+                    const bool own = MODE == kHess && gy >= oy0 && gy < oy0 + TOH && gy < H && gx >= xs && gx < xe;
                     if (!mbar_wait(&S.bar[B_FWD + (g & 1)], (g >> 1) & 1, abort_flag, status)) break;
                     fence_after();
                     const uint32_t rc = tmem + lane_base + 64 * (g & 1);
-                    const int gy = oy0 - 3 + 4 * t + q;
-                    const uint32_t keep = (interior || (gy >= 0 && gy < H && gx >= 0 && gx < W)) ? 0xFFFFFFFFu : 0u;
                     if (TF) {
                         // Psi takes R's columns one for one: two halves of 24 filters keep the registers low
 #pragma unroll
@@ -547,10 +567,30 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                             tmem_ld8(rc + 24 * hh + 16, r + 16);
                             tmem_wait_ld();
                             uint32_t w[24];
+                            if constexpr (MODE == kHvp) {
+                                // the Hessian applied to the direction: (rho''(K_i u) / 2) (K_i p) (2 alpha_i in Wa)
 #pragma unroll
-                            for (int j = 0; j < 24; ++j) {
-                                const float r0 = r[j];
-                                w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
+                                for (int j = 0; j < 24; ++j) w[j] = to_tf32(r[j] * fh[24 * hh + j]) & keep;
+                            } else if constexpr (MODE == kHess) {
+                                float fac[24];
+#pragma unroll
+                                for (int j = 0; j < 24; ++j) {
+                                    const float r0 = r[j], inv = rcp_approx(fmaf(r0, r0, 1.0f));
+                                    fac[j] = fmaf(-r0, r0, 1.0f) * inv * inv;
+                                    w[j] = 0u;
+                                }
+                                if (own) {
+                                    float4 *fo = reinterpret_cast<float4 *>(D.hess + ((size_t)gy * W + gx) * 48 + 24 * hh);
+#pragma unroll
+                                    for (int j = 0; j < 6; ++j)
+                                        fo[j] = make_float4(fac[4 * j], fac[4 * j + 1], fac[4 * j + 2], fac[4 * j + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 24; ++j) {
+                                    const float r0 = r[j];
+                                    w[j] = to_tf32(r0 * rcp_approx(fmaf(r0, r0, 1.0f))) & keep;
+                                }
                             }
                             tmem_st16(rc + 24 * hh, w);
                             tmem_st8(rc + 24 * hh + 16, w + 16);
@@ -671,6 +711,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_foe_tc(const __grid_constant__ Laun
                 const size_t idx = (size_t)(oy0 + r) * ld + gx;
                 if (MODE == kGrad) {
                     D.out[idx] = g[k2] + data_grad(uh[k2], S.O[1][j], D.model, D.sc.lambda);
+                } else if (MODE == kHvp) {
+                    // H_E p = H_prior p + lambda p (the quadratic data term of the Anscombe-L2 model)
+                    D.out[idx] = g[k2] + D.sc.lambda * uh[k2];
+                } else if (MODE == kHess) {
+                    // factors only
                 } else {
                     float nh, nd;
                     ipiano_update_f32(g[k2], uh[k2], S.O[0][j], S.O[1][j], D.model, D.sc, nh, nd);
@@ -762,13 +807,15 @@ cudaError_t tc_setup()
     if ((e = tc_attr<kGrad, false, kShortH>())) return e;
     if ((e = tc_attr<kStep, true, kShortH>())) return e;
     if ((e = tc_attr<kGrad, true, kShortH>())) return e;
+    if ((e = tc_attr<kHvp, true, kShortH>())) return e;
+    if ((e = tc_attr<kHess, true, kShortH>())) return e;
     return pair_setup();
 }
 
 cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s, const SideStream &side)
 {
     if (a.nimg <= 0 || a.tile_prefix[a.nimg] <= 0) return cudaSuccess;
-    if (mode != kStep && mode != kGrad) return cudaErrorNotSupported;
+    if (mode != kStep && mode != kGrad && !(tf32 && (mode == kHvp || mode == kHess))) return cudaErrorNotSupported;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -799,8 +846,10 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     const int tiles = b.tile_prefix[b.nimg];
     // persistent CTAs: as many as are resident at once (tensor memory admits two per SM)
     const int grid = std::min(tiles, 2 * sms);
-    if (tf32) e = mode == kStep ? tc_launch_one<kStep, true, kShortH>(b, grid, d_status, s26)
-                                : tc_launch_one<kGrad, true, kShortH>(b, grid, d_status, s26);
+    if (tf32) e = mode == kStep  ? tc_launch_one<kStep, true, kShortH>(b, grid, d_status, s26)
+                  : mode == kGrad ? tc_launch_one<kGrad, true, kShortH>(b, grid, d_status, s26)
+                  : mode == kHvp  ? tc_launch_one<kHvp, true, kShortH>(b, std::min(tiles, sms), d_status, s26)
+                                  : tc_launch_one<kHess, true, kShortH>(b, std::min(tiles, sms), d_status, s26);
     else e = mode == kStep ? tc_launch_one<kStep, false, kShortH>(b, grid, d_status, s26)
                            : tc_launch_one<kGrad, false, kShortH>(b, grid, d_status, s26);
     if (e != cudaSuccess || !both) return e;

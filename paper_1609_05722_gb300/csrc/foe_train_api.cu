@@ -177,7 +177,11 @@ extern "C" foe_status foe_train_grad_implicit(foe_ctx *c, const float *clean, co
     if ((st = check_opts_fixed(c, o, "foe_train_grad_implicit")) != FOE_OK) return st;
     if ((st = check_no_tol(c, o, "foe_train_grad_implicit")) != FOE_OK) return st;
     if (o->model != FOE_MODEL_ANS_L2) { set_err(c, "training needs FOE_MODEL_ANS_L2"); return FOE_EUNSUPPORTED; }
-    if (o->prec != FOE_PREC_FP32) { set_err(c, "training runs in FP32"); return FOE_EUNSUPPORTED; }
+    if (o->prec != FOE_PREC_FP32 && o->prec != FOE_PREC_TF32) {
+        set_err(c, "foe_train_grad_implicit runs in FP32, or with TF32 tensor-core Hessian-vector products");
+        return FOE_EUNSUPPORTED;
+    }
+    const bool tc_hvp = o->prec == FOE_PREC_TF32;
     if (B < 1 || !dfilters || !dlogalpha) { set_err(c, "need B >= 1 and gradient buffers"); return FOE_EINVAL; }
     if (max_cg < 1 || !(cg_tol >= 0.0f) || !std::isfinite(cg_tol)) {
         set_err(c, "need max_cg >= 1 and a finite cg_tol >= 0");
@@ -236,6 +240,51 @@ extern "C" foe_status foe_train_grad_implicit(foe_ctx *c, const float *clean, co
             if ((st = forward_group(c, d, i0, std::min(B, i0 + group), o->bc, s)) != FOE_OK) return st;
     }
     auto wstar = [&](int i) -> const float * { return (T & 1) ? slot[i].uh1 : slot[i].uh0; };
+
+    // ---- TF32 path: the Hessian factors (1 - r^2) / (1 + r^2)^2 of the responses of w*, once ----
+    const size_t hess_per = (size_t)H * W * 48;
+    std::vector<ImgDesc> hd;
+    if (tc_hvp) {
+        const size_t hb = (size_t)B * hess_per * sizeof(float);
+        if (hb > c->hess_bytes) {
+            if (c->d_hess) FOE_CUDA(c, cudaFree(c->d_hess));
+            c->d_hess = nullptr;
+            c->hess_bytes = 0;
+            FOE_CUDA(c, cudaMalloc(&c->d_hess, hb));
+            c->hess_bytes = hb;
+        }
+        hd.resize(B);
+        for (int i = 0; i < B; ++i) {
+            hd[i] = ImgDesc{};
+            hd[i].u_hi[0] = const_cast<float *>(wstar(i));
+            hd[i].H = H;
+            hd[i].W = W;
+            hd[i].ld = ld;
+            hd[i].model = foe::kAnsL2;
+            hd[i].sc = sc;
+            hd[i].hess = c->d_hess + (size_t)i * hess_per;
+        }
+        for (int i0 = 0; i0 < B; i0 += group) {
+            args_begin(c, o->bc);
+            for (int i = i0; i < std::min(B, i0 + group); ++i) args_add(c, FOE_PREC_TF32, hd[i]);
+            if ((st = launch(c, FOE_PREC_TF32, foe::kHess, s)) != FOE_OK) return st;
+        }
+    }
+    // H_E x on the tensor cores: the direction's responses (TF32), times the stored factors, the adjoint, + lambda x
+    auto tc_hvp_launch = [&](const float *x, float *out) -> foe_status {
+        for (int i0 = 0; i0 < B; i0 += group) {
+            args_begin(c, o->bc);
+            for (int i = i0; i < std::min(B, i0 + group); ++i) {
+                ImgDesc e = hd[i];
+                e.u_hi[0] = const_cast<float *>(x + (size_t)i * plane);
+                e.out = out + (size_t)i * plane;
+                args_add(c, FOE_PREC_TF32, e);
+            }
+            foe_status r = launch(c, FOE_PREC_TF32, foe::kHvp, s);
+            if (r != FOE_OK) return r;
+        }
+        return FOE_OK;
+    };
 
     // ---- loss and b = dL/dw at w* ----
     for (int i = 0; i < B; ++i)
@@ -296,7 +345,7 @@ extern "C" foe_status foe_train_grad_implicit(foe_ctx *c, const float *clean, co
     int K = 0;  // iterations launched; every image's final <r, r> is then in slot K & 1
     for (int k = 0; k < max_cg; ++k) {
         if (k % 32 == 0 && all_done(k)) break;
-        if ((st = bwd(true, pv, Apv)) != FOE_OK) return st;
+        if ((st = tc_hvp ? tc_hvp_launch(pv, Apv) : bwd(true, pv, Apv)) != FOE_OK) return st;
         FOE_CUDA(c, foe::launch_cg_dot(pv, Apv, B, H, W, ld, part_pap, s));
         FOE_CUDA(c, foe::launch_cg_update(qv, rv, pv, Apv, B, H, W, ld, part_pap, part_rr, cgs, k, tol2, s));
         K = k + 1;

@@ -171,3 +171,35 @@ def test_lbfgs_on_the_device_follows_the_oracle_driven_trajectory(setup):
     assert Lo[-1] < 0.99 * Lo[0]
     assert torch.linalg.vector_norm(kd - ko) <= 1e-2 * torch.linalg.vector_norm(ko - k0)
     assert torch.linalg.vector_norm(lad - lao) <= 1e-2 * torch.linalg.vector_norm(lao - la0)
+
+
+@pytest.mark.parametrize("shape,bc", [((40, 33), F.FOE_BC_SYMMETRIC), ((64, 60), F.FOE_BC_ZERO)])
+def test_implicit_gradient_with_tensor_core_hessian_products(setup, shape, bc):
+    # opts.prec = TF32: the CG's Hessian-vector products on the tensor cores (TF32 operands: the direction's
+    # responses and the curvature-weighted products are rounded to 10-bit mantissas, about 5e-4 each), the rest
+    # FP32.  The gradients follow the oracle's to 1e-3 of their largest component (measured 2e-4), the loss exactly as
+    # the FP32 path
+    # (the same lower-level solve), and the CG converges on the TF32 operator.
+    k, a, ctx = setup
+    H, W = shape
+    Bn, T = 2, 150
+    clean, noisy, cd, nd, ld = batch(Bn, H, W, 4.0, 850 + H)
+    tau, _ = F.foe_step_size(ctx, bc, GAMMA)
+    L32, dk32, da32, rep32 = implicit(ctx, cd, nd, Bn, H, W, ld, T, tau, bc)
+    dk = torch.zeros((48, 49), dtype=torch.float32, device="cuda")
+    da = torch.zeros((48,), dtype=torch.float32, device="cuda")
+    o = F.SolveOpts(model=F.FOE_MODEL_ANS_L2, prec=F.FOE_PREC_TF32, iters=T, tau=tau, bc=bc, lam=1.0, gamma=GAMMA)
+    L, rep = F.foe_train_grad_implicit(ctx, cd, nd, Bn, H, W, ld, o, dk, da, 500, 1e-5)
+    torch.cuda.synchronize()
+    dk = dk.cpu().numpy().astype(np.float64).reshape(48, 7, 7)
+    da = da.cpu().numpy().astype(np.float64)
+    pr = O.Problem(k.astype(np.float64), a.astype(np.float64), H, W, bc=bc, model=O.MODEL_ANS_L2, lam=1.0, tau=tau,
+                   gamma=GAMMA)
+    Lr, dkr, dar, _, _ = pr.train_grad_implicit(clean, noisy, T, 2000, 1e-12)
+    ek = np.abs(dk - dkr).max() / np.abs(dkr).max()
+    ea = np.abs(da - dar).max() / np.abs(dar).max()
+    print(f"implicit TF32 {shape} bc={bc}: CG {rep['cg_iters']} it (FP32 {rep32['cg_iters']}), relres "
+          f"{rep['cg_relres']:.1e}; dk err {ek:.1e}, dlogalpha err {ea:.1e}")
+    assert L == L32 and L == pytest.approx(Lr, rel=1e-5)
+    assert rep["breakdowns"] == 0 and rep["cg_relres"] <= 1e-5
+    assert ek <= 1e-3 and ea <= 1e-3
