@@ -171,7 +171,7 @@ FOE_API int foe_step_log(const foe_ctx *ctx, float *tau, unsigned char *accepted
  * taken on the device: an iteration is one CUDA graph launch (gradient, snapshot, then a conditional loop of
  * trials that a one-thread kernel ends by accepting), all iterations are queued without waiting, and the host
  * synchronises once at the end.  A trial costs a step, an energy evaluation and two reductions, so this mode is
- * for accuracy, not throughput.
+ * for accuracy, not throughput.  Not on a stream under capture (FOE_EUNSUPPORTED).
  * foe_step_log returns the trials of the last such solve.
  * With opts.tol > 0 (fixed steps) the host reads the image's stopping word one check interval behind the
  * device (an event on the stream; the next interval is queued meanwhile), issues no launch past the interval

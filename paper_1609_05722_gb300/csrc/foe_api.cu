@@ -235,6 +235,15 @@ static foe_status denoise_backtrack(foe_ctx *c, const float *y, float *x, int H,
         set_err(c, "FOE_STEP_BACKTRACK needs FOE_PREC_FP32");
         return FOE_EUNSUPPORTED;
     }
+    {
+        // the iterations are graphs with conditional nodes, which cannot become part of another graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        FOE_CUDA(c, cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_err(c, "FOE_STEP_BACKTRACK cannot run on a stream under capture");
+            return FOE_EUNSUPPORTED;
+        }
+    }
     foe_status st;
     const size_t plane = (size_t)H * ld;
     if ((st = ensure_ws(c, 8 * plane * sizeof(float))) != FOE_OK) return st;
