@@ -26,11 +26,12 @@ struct SideStream {
     cudaEvent_t fork, join;
 };
 cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, cudaStream_t s, const SideStream &side);
-int pair_tile();
+int pair_tile_w();  // output columns and rows of the pixel-pair tiles
+int pair_tile_h();
 int pair_min_rows();
 long pair_min_pixels();
 cudaError_t pair_setup();
-// the images of `a` tiled pair_tile() x pair_tile() (all of them if `all`), one persistent CTA per SM
+// the images of `a` in pixel-pair tiles (all of them if `all`), one persistent CTA per SM
 cudaError_t pair_launch(const LaunchArgs &a, int mode, bool all, int sms, int *d_status, cudaStream_t s);
 
 // Backward pass of the unrolled solve (foe_train.cu).

@@ -1,9 +1,14 @@
 // Pixel-pair tensor-core FoE step kernel for sm_103a (BF16 operands, kind::f16, FP32 accumulators in tensor
-// memory): one iPiano step (Eq. iPianoupdate) per launch over 58 x 58 output tiles, one persistent CTA per SM.
+// memory): one iPiano step (Eq. iPianoupdate) per launch over output tiles of 58 columns x 66 rows, one persistent
+// CTA per SM.
 //
 // The prior gradient sum_i alpha_i K_i^T rho'(K_i u) (Eq. FoEF) of a tile needs the responses on the tile plus a
-// 3-pixel ring: a response region of 64 x 64 pixels.  Each tensor-memory lane holds two horizontally adjacent
-// response pixels (a pair), so an M-tile of 128 lanes is 4 response rows of 32 pairs and a tile is 16 M-tiles.
+// 3-pixel ring: a response region of 64 columns x 72 rows.  Each tensor-memory lane holds two horizontally adjacent
+// response pixels (a pair), so an M-tile of 128 lanes is 4 response rows of 32 pairs and a tile is 18 M-tiles.  The
+// width is fixed by the 32 pairs of a lane quarter; the height is a choice: 66 rows against 58 (16 M-tiles) cut the
+// ten-image 512^2 benchmark step from 28.6 to 27.1 ms (720 tiles per launch fill 5 waves of 152 CTAs, 810 filled
+// 6) and 64 uneven images from 29.1 to 29.7 k MPix.iter/s, while a lone 512^2 image (one wave either way) takes
+// 7.9 ms against 7.2 ms and five 512^2 images 17.4 against 15.9 ms.
 //
 //   forward  R[m][n] = sum_k E-window(m)[k] Wf[n][k]        M = 128 pairs, N = 96 = 2 pixels x 48 filters,
 //            K = 64 = 8 tap rows x 8 columns: the 8 columns cover the 7 taps of both pixels of a pair, and the
@@ -55,13 +60,16 @@ namespace {
 
 using namespace ptx;
 
-constexpr int PT = 58;               // output tile side
-constexpr int PRR = PT + 6;          // response rows (and columns): 64
-constexpr int PNMT = PRR / 4;        // M-tiles per tile
-constexpr int PER = PRR + 7;         // E rows = input rows: 7 tap rows + the zero-weight eighth (71)
+constexpr int PTX = 58;              // output tile width (32 pairs of response columns, less the 3-pixel ring)
+constexpr int PTY = 66;              // output tile height
+constexpr int PRX = PTX + 6;         // response columns: 64
+constexpr int PRY = PTY + 6;         // response rows
+constexpr int PNMT = PRY / 4;        // M-tiles per tile
+constexpr int PER = PRY + 7;         // E rows = input rows: 7 tap rows + the zero-weight eighth
+static_assert(PRX == 64 && PRY % 4 == 0, "tile geometry");
 constexpr int PUW = 70;              // input columns used: 64 response columns + 6
 constexpr int PUC = 76;              // floats per staged input row (the TMA box: 70 + up to 3 of alignment slack)
-constexpr int kPairMinRows = PT + 1; // images of fewer rows keep the 26 x 26 tiles
+constexpr int kPairMinRows = PTY + 1; // images of fewer rows keep the 26 x 26 tiles
 constexpr int NRST = 3;              // response stages R (96 columns each)
 constexpr int NPST = 2;              // Psi stages (48 columns each)
 constexpr int NZST = 2;              // Z2 stages (64 columns each)
@@ -92,12 +100,12 @@ constexpr int B_ADJ = 12;     // [NZST] adjoint MMAs of g complete: Z2(g) ready 
 constexpr int B_ZFREE = 15;   // [NZST] Z2(g) loaded by every col2im thread                   count 128
 constexpr int B_EREADY = 18;  // [2] E buffer b built                                         count NSTG
 constexpr int B_EFREE = 20;   // [2] every forward MMA reading E buffer b complete            count 1 (commit)
-constexpr int B_CDONE = 22;   // [2][16] col2im of M-tile t of the tile in buffer b emitted   count 128
-constexpr int B_GFREE = 54;   // [2] output pass done with partial-sum buffer b               count 128
-constexpr int B_ULAND = 56;   // input region landed (TMA bytes, or every staging copy)       count NSTG
-constexpr int B_W = 57;       // filter operand images landed                                 count 1 + tx
-constexpr int B_DRAIN = 58;   // [2] all MMAs of the forward / adjoint issuer complete        count 1 (commit)
-constexpr int NBAR = 60;
+constexpr int B_CDONE = 22;   // [2][PNMT] col2im of M-tile t of the tile in buffer b emitted count 128
+constexpr int B_GFREE = B_CDONE + 2 * PNMT;  // [2] output pass done with partial-sum buffer b  count 128
+constexpr int B_ULAND = B_GFREE + 2;  // input region landed (TMA bytes, or every staging copy) count NSTG
+constexpr int B_W = B_ULAND + 1;      // filter operand images landed                         count 1 + tx
+constexpr int B_DRAIN = B_W + 1;      // [2] all MMAs of the forward / adjoint issuer complete count 1 (commit)
+constexpr int NBAR = B_DRAIN + 2;
 static_assert(NRST <= 3 && NPST <= 3 && NZST <= 3, "barrier slots");
 
 struct PairSmem {
@@ -105,7 +113,7 @@ struct PairSmem {
     uint4 E[2][PER * 32];                // forward A operand: entry (row i, pair j) = bf16 u(i, 2j .. 2j+7) - mean
     uint4 Wf[WF_ENT];
     uint4 Wa[WA_ENT];
-    uint4 G[2][PRR][32];                 // vertical col2im partials: [buffer][output row][pair], the f16x2 words of
+    uint4 G[2][PRY][32];                 // vertical col2im partials: [buffer][output row][pair], the f16x2 words of
                                          // the four lane quarters in one 16-byte entry
     float O[kORing][3][2][128];          // output-pass operands (u, delta, d of both pixels) of the next steps
     int tprefix[kMaxBatch + 1];
@@ -134,17 +142,18 @@ struct Geo {
     int im, oy0, ox0, ys, ye, xs, xe, H, W;
 };
 
-// Origin and write range of a tile along one axis of length L.  The last tile is placed flush with the far border,
-// so that the reflections of the pixels within 3 of that border lie inside its response region; the tile before it
-// writes only up to max(L - 58, 3), which keeps the pixels within 3 of the near border in the first tile (origin 0)
-// when the flush tile starts at 1 or 2 (L = 59, 60).
+// Origin and write range of a tile of P outputs along one axis of length L.  The last tile is placed flush with the
+// far border, so that the reflections of the pixels within 3 of that border lie inside its response region; the tile
+// before it writes only up to max(L - P, 3), which keeps the pixels within 3 of the near border in the first tile
+// (origin 0) when the flush tile starts at 1 or 2 (L = P + 1, P + 2).
+template <int P>
 __device__ __forceinline__ void pair_axis(int t, int n, int L, int &o, int &s, int &e)
 {
-    o = t * PT;
+    o = t * P;
     s = o;
-    e = min(o + PT, L);
-    if (L > PT) {
-        const int last = L - PT, split = max(last, 3);
+    e = min(o + P, L);
+    if (L > P) {
+        const int last = L - P, split = max(last, 3);
         o = min(o, last);
         s = t + 1 < n ? o : split;
         e = t + 1 < n ? min(e, split) : L;
@@ -177,9 +186,9 @@ __device__ __forceinline__ Geo pair_geometry(const PairSmem &S, int nimg, int ti
     const int tiles_x = S.timg[lo][0];
     g.H = S.timg[lo][1];
     g.W = S.timg[lo][2];
-    const int tiles_y = (g.H + PT - 1) / PT, lt = tile - S.tprefix[lo];
-    pair_axis(lt % tiles_x, tiles_x, g.W, g.ox0, g.xs, g.xe);
-    pair_axis(lt / tiles_x, tiles_y, g.H, g.oy0, g.ys, g.ye);
+    const int tiles_y = (g.H + PTY - 1) / PTY, lt = tile - S.tprefix[lo];
+    pair_axis<PTX>(lt % tiles_x, tiles_x, g.W, g.ox0, g.xs, g.xe);
+    pair_axis<PTY>(lt / tiles_x, tiles_y, g.H, g.oy0, g.ys, g.ye);
     return g;
 }
 
@@ -251,10 +260,10 @@ __device__ __forceinline__ bool group_all(int id, bool ok)
 
 __device__ __forceinline__ bool prod_all(bool ok) { return group_all<NSTG>(kBarProd, ok); }
 
-// Sum of the four partial rows at region position (Y, X), any position of the 64 x 64 region (padding fold).
+// Sum of the four partial rows at region position (Y, X), any position of the response region (padding fold).
 __device__ __forceinline__ float g_at(const uint4 (*Gb)[32], int Y, int X)
 {
-    if (Y < 0 || Y >= PRR || X < 0 || X >= PRR) return 0.0f;
+    if (Y < 0 || Y >= PRY || X < 0 || X >= PRX) return 0.0f;
     const uint4 e = Gb[Y][X >> 1];
     const uint32_t w[4] = {e.x, e.y, e.z, e.w};
     float s = 0.0f;
@@ -371,7 +380,7 @@ __device__ __forceinline__ OutCols out_cols(const Geo &g, int n)
     c.gx0 = g.ox0 + 2 * c.j - 3;
     const int X0 = 2 * c.j, gx1 = c.gx0 + 1;
     c.c0 = p < 120 && X0 >= 3 && c.gx0 >= g.xs && c.gx0 < g.xe;
-    c.c1 = p < 120 && X0 + 1 <= PT + 2 && gx1 >= g.xs && gx1 < g.xe;
+    c.c1 = p < 120 && X0 + 1 <= PTX + 2 && gx1 >= g.xs && gx1 < g.xe;
     auto mirror = [&](int gx) {
         const int m = gx < 3 ? -1 - gx : (gx >= g.W - 3 ? 2 * g.W - 1 - gx : -1000);
         return m == -1000 ? -1 : m - g.ox0 + 3;
@@ -386,7 +395,7 @@ __device__ __forceinline__ bool out_row(const Geo &g, const OutCols &c, int t, i
 {
     Y = 4 * t - 3 + c.r4;
     gy = g.oy0 + Y - 3;
-    return Y >= 3 && Y <= PT + 2 && gy >= g.ys && gy < g.ye;
+    return Y >= 3 && Y <= PTY + 2 && gy >= g.ys && gy < g.ye;
 }
 
 template <int MODE>
@@ -565,7 +574,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         bool ok = true;
         for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride)) {
             const Geo g = pair_geometry(S, A.nimg, tile);
-            const bool interior = g.oy0 >= 3 && g.ox0 >= 3 && g.oy0 + PT + 3 <= g.H && g.ox0 + PT + 3 <= g.W;
+            const bool interior = g.oy0 >= 3 && g.ox0 >= 3 && g.oy0 + PTY + 3 <= g.H && g.ox0 + PTX + 3 <= g.W;
             const int gx0 = g.ox0 - 3 + 2 * lane;
             for (int t = 0; t < PNMT; ++t, ++gm) {
                 if (!mbar_wait_warp(&S.bar[B_FWD + rs], rph, abort_flag, status)) {
@@ -642,7 +651,7 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
             uint32_t *Gq = reinterpret_cast<uint32_t *>(&S.G[b][0][0]) + q;  // word q of entry (Y, pair)
             uint64_t c0 = 0, c1 = 0, c2 = 0;  // carried partial sums of output rows y + 1 .. y + 3 (f32 pairs)
             auto emit = [&](int Y, uint64_t v) {
-                if (Y >= 0 && Y < PRR) {
+                if (Y >= 0 && Y < PRY) {
                     float lo, hi;
                     f2_unpack(v, lo, hi);
                     Gq[4 * (Y * 32 + lane)] = pack_f16x2(lo, hi);
@@ -893,7 +902,8 @@ thread_local PairArgs t_args;
 
 }  // namespace
 
-int pair_tile() { return PT; }
+int pair_tile_w() { return PTX; }
+int pair_tile_h() { return PTY; }
 int pair_min_rows() { return kPairMinRows; }
 long pair_min_pixels() { return 90000; }
 
@@ -928,7 +938,7 @@ cudaError_t pair_launch(const LaunchArgs &a, int mode, bool all, int sms, int *d
     cudaError_t e;
     for (int i = 0; i < a.nimg; ++i) {
         const ImgDesc &d = a.img[i];
-        if (!all && d.tile_h != PT) continue;
+        if (!all && d.tile_h != PTY) continue;
         p.img[p.nimg] = d;
         p.tile_prefix[p.nimg + 1] = p.tile_prefix[p.nimg] + (a.tile_prefix[i + 1] - a.tile_prefix[i]);
         for (int par = 0; par < 2; ++par)

@@ -787,7 +787,7 @@ cudaError_t tc_attr()
 
 }  // namespace
 
-// BF16 images of at least pair_min_rows() rows and pair_min_pixels() pixels take the pixel-pair kernel's 58 x 58 tiles;
+// BF16 images of at least pair_min_rows() rows and pair_min_pixels() pixels take the pixel-pair kernel's tiles;
 // the rest take 26 x 26 tiles.  The pair kernel runs one CTA per SM and a tile in about 20 us; the 26 x 26 kernel
 // runs two CTAs per SM and a tile in about 10 us, so it finishes small images sooner (300 iterations: 256^2 alone
 // 3.7 ms against 7.1 ms) while the pair kernel does more per SM once there is enough work (five 512^2 images together:
@@ -796,9 +796,9 @@ cudaError_t tc_attr()
 // alone, so an image is tiled, and rounded, the same way in any batch.
 int tc_tile_h(bool tf32, int H, int W)
 {
-    return !tf32 && H >= pair_min_rows() && (long)H * W >= pair_min_pixels() ? pair_tile() : kShortH;
+    return !tf32 && H >= pair_min_rows() && (long)H * W >= pair_min_pixels() ? pair_tile_h() : kShortH;
 }
-int tc_tile_w(int tile_h) { return tile_h == pair_tile() ? pair_tile() : TO; }
+int tc_tile_w(int tile_h) { return tile_h == pair_tile_h() ? pair_tile_w() : TO; }
 
 cudaError_t tc_setup()
 {
@@ -820,12 +820,12 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // images tiled 58 x 58 run in the pixel-pair kernel (foe_pair.cu), the others (26 x 26 tiles, and every TF32
+    // images in pixel-pair tiles run in the pixel-pair kernel (foe_pair.cu), the others (26 x 26 tiles, and every TF32
     // image) here; a launch holding both kinds runs one launch of each kernel at the same time: the 26 x 26 kernel
     // on the side stream, forked after the work queued so far and joined back before whatever is queued next, so that
     // each kernel's CTAs take the SMs that the other leaves free (one pair CTA or two 26 x 26 CTAs fit an SM)
     int npair = 0;
-    for (int i = 0; i < a.nimg; ++i) npair += a.img[i].tile_h == pair_tile();
+    for (int i = 0; i < a.nimg; ++i) npair += a.img[i].tile_h == pair_tile_h();
     const bool both = npair > 0 && npair < a.nimg;
     if (both) {
         if ((e = cudaEventRecord(side.fork, s)) != cudaSuccess) return e;
@@ -838,7 +838,7 @@ cudaError_t tc_launch(const LaunchArgs &a, int mode, bool tf32, int *d_status, c
     b.nimg = 0;
     b.tile_prefix[0] = 0;
     for (int i = 0; i < a.nimg; ++i) {
-        if (a.img[i].tile_h == pair_tile()) continue;
+        if (a.img[i].tile_h == pair_tile_h()) continue;
         b.img[b.nimg] = a.img[i];
         b.tile_prefix[b.nimg + 1] = b.tile_prefix[b.nimg] + (a.tile_prefix[i + 1] - a.tile_prefix[i]);
         b.nimg++;

@@ -74,12 +74,12 @@ def problem(bank32, H, W, model, bc, tau):
 # Images below 90000 pixels or 59 rows (and every TF32 image) take 26 x 26 tiles: widths 54 and 79 leave a last tile
 # of 2 and 1 columns after full 26-column tiles, where the reflection of a pixel within 3 columns of the right border
 # falls outside a 32-column response region that does not reach it; width 28 puts the flush last tile at column 2,
-# so the columns within 3 of the left border must stay with the first tile.  Larger BF16 images take the 58 x 58
-# pixel-pair tiles (PAIR_SHAPES, long strips so that the small side sets the case): 59 / 60 rows or columns put the
-# flush last tile at 1 / 2 (the same split rule in both directions), 117, 122 and 456 leave ragged flush tiles, 30
-# and 33 are narrower than one tile.
-PAIR_SHAPES = [(3440, 59), (59, 3400), (3335, 60), (60, 3340), (1720, 117), (122, 1650), (6700, 30), (6100, 33),
-               (456, 456)]
+# so the columns within 3 of the left border must stay with the first tile.  Larger BF16 images (at least 67 rows)
+# take the pixel-pair tiles of 58 columns x 66 rows (PAIR_SHAPES, long strips so that the small side sets the case):
+# 59 / 60 columns and 67 / 68 rows put the flush last tile at 1 / 2 (the same split rule in both directions), 117,
+# 122, 135 and 456 leave ragged flush tiles, 30 and 33 columns are narrower than one tile.
+PAIR_SHAPES = [(3440, 59), (67, 3000), (3335, 60), (68, 2950), (1720, 117), (122, 1650), (6700, 30), (6100, 33),
+               (456, 456), (135, 1490)]
 SHAPES = [(64, 64), (13, 17), (37, 70), (96, 33), (7, 7), (130, 200), (53, 54), (28, 79), (240, 70), (233, 30),
           (40, 28), (59, 60), (60, 59), (61, 122), (120, 117), (116, 59)] + PAIR_SHAPES
 
@@ -110,7 +110,7 @@ def test_tc_gradient(dev, ctx, bank32, shape, bc, model, prec):
 
 @pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("shape", [(64, 64), (37, 70), (7, 7), (30, 54), (245, 61), (60, 59), (150, 130), (3335, 60),
-                                   (59, 3400), (456, 456)])
+                                   (67, 3000), (456, 456)])
 @pytest.mark.parametrize("model", [F.FOE_MODEL_DIRECT, F.FOE_MODEL_ANS_L2, F.FOE_MODEL_ANS_IDIV])
 def test_tc_single_step(dev, ctx, bank32, shape, model, prec):
     H, W = shape
