@@ -367,6 +367,22 @@ FOE_API foe_status foe_server_get_stats(const foe_server *srv, foe_server_stats 
 FOE_API foe_status foe_profile(foe_ctx *ctx, int enable);
 FOE_API foe_status foe_profile_read(foe_ctx *ctx, double *loop_ms, long *launches, double *pixel_iters);
 
+/* Tensor-core cost probe (diagnostic, no context): SM cycles per tcgen05.mma of kind::f16 (BF16 operands, FP32
+ * accumulator in tensor memory, K = 16 per MMA) for an M x N shape: the contraction ceiling of the kernels that
+ * compute the responses K_i u and their adjoint (Eq. FoEF) as implicit GEMMs.  Measured with clock64 over `count`
+ * MMAs per issuing warp (1 or 2 warps, each into its own accumulator; operands cycle over a K = 64 region); the
+ * second of two passes is reported.
+ *   m, n            one CTA: m = 64 (n a multiple of 8 in 8..256) or m = 128 (n a multiple of 16 in 16..256);
+ *                   cta_pair = 1: m = 256 over the two SMs of a two-CTA cluster (cta_group::2; each SM holds 128
+ *                   rows of A and n / 2 rows of B), n a multiple of 16 in 32..256
+ *   a_in_tmem       1: the A operand is read from tensor memory (m = 128, one CTA), else from shared memory
+ *   issuers, count  1 or 2 issuing warps; MMAs per warp, 1..65536
+ *   cycles_per_mma  host, out: elapsed cycles / (issuers x count)
+ * FOE_EINVAL for other arguments, FOE_EUNSUPPORTED on a device of another compute capability than 10.3,
+ * FOE_ETIMEOUT if the bounded wait for the MMAs expired.  Synchronises the current device. */
+FOE_API foe_status foe_mma_cost(int m, int n, int a_in_tmem, int cta_pair, int issuers, int count,
+                                double *cycles_per_mma);
+
 FOE_API const char *foe_status_string(foe_status s);
 
 /* Device-side status of the context: every wait of the tensor-core kernel is bounded, and one that expires records

@@ -103,6 +103,7 @@ def lib() -> C.CDLL:
                                             vp, C.POINTER(foe_implicit_report), vp]),
             "foe_profile": (i, [vp, i]),
             "foe_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_long), C.POINTER(d)]),
+            "foe_mma_cost": (i, [i, i, i, i, i, i, C.POINTER(d)]),
             "foe_status_string": (C.c_char_p, [i]),
             "foe_last_error": (C.c_char_p, [vp]),
         }
@@ -323,6 +324,14 @@ def foe_profile_read(ctx) -> tuple[float, int, float]:
     ms, n, px = C.c_double(), C.c_long(), C.c_double()
     _check(lib().foe_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(px)), ctx, "foe_profile_read")
     return ms.value, n.value, px.value
+
+
+def foe_mma_cost(m: int, n: int, a_in_tmem: bool = False, cta_pair: bool = False, issuers: int = 2,
+                 count: int = 4096) -> float:
+    """SM cycles per tcgen05.mma (kind::f16, K = 16) of an m x n shape; see include/foe.h."""
+    out = C.c_double()
+    _check(lib().foe_mma_cost(m, n, int(a_in_tmem), int(cta_pair), issuers, count, C.byref(out)), what="foe_mma_cost")
+    return out.value
 
 
 # ---- continuous-batching server ----

@@ -78,3 +78,13 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, bank):
     assert lib.foe_denoise(None, 16, 16, 64, 64, 64, 4.0, C.byref(o), None, None) == F.FOE_EINVAL
     assert lib.foe_energy_grad(None, 16, 16, 64, 64, 64, 1, 1.0, 0, 0, None, None, None) == F.FOE_EINVAL
     assert lib.foe_anscombe(None, None, -1, None) == F.FOE_EINVAL
+
+
+@pytest.mark.parametrize("args", [(100, 64, 0, 0, 2, 16), (128, 40, 0, 0, 2, 16), (64, 60, 0, 0, 2, 16),
+                                  (64, 64, 1, 0, 2, 16), (128, 256, 1, 0, 2, 16), (128, 64, 0, 1, 2, 16),
+                                  (256, 64, 1, 1, 2, 16), (128, 64, 0, 0, 3, 16), (128, 64, 0, 0, 2, 0)])
+def test_mma_cost_rejects_bad_shapes_on_the_host(lib, args):
+    # checked before any device call, so this runs without a GPU
+    out = C.c_double(-1.0)
+    assert lib.foe_mma_cost(*args, C.byref(out)) == F.FOE_EINVAL
+    assert out.value == -1.0
