@@ -398,15 +398,38 @@ __device__ __forceinline__ bool out_row(const Geo &g, const OutCols &c, int t, i
     return Y >= 3 && Y <= PTY + 2 && gy >= g.ys && gy < g.ye;
 }
 
+// The image's planes and step constants, read once per tile from the launch parameters (the output pass would
+// otherwise re-read them at every step).
+struct OutImg {
+    const float *u, *d;                  // u^n (this step's plane), data
+    float *un, *dl, *out;                // u^{n+1} (the other plane), delta, gradient (kGrad)
+    int ld, model;
+    StepConsts sc;
+};
+
+__device__ __forceinline__ OutImg out_img(const PairArgs &A, int im)
+{
+    const ImgDesc &D = A.img[im];
+    OutImg o;
+    o.u = D.u_hi[A.parity];
+    o.un = D.u_hi[A.parity ^ 1];
+    o.d = D.d;
+    o.dl = D.delta;
+    o.out = D.out;
+    o.ld = D.ld;
+    o.model = D.model;
+    o.sc = D.sc;
+    return o;
+}
+
 template <int MODE>
-__device__ __forceinline__ void out_fetch(const PairArgs &A, const Geo &g, const OutCols &c, float (*O)[2][128], int t,
+__device__ __forceinline__ void out_fetch(const OutImg &o, const Geo &g, const OutCols &c, float (*O)[2][128], int t,
                                           int p)
 {
     int Y, gy;
     if (t < PNMT && out_row(g, c, t, Y, gy) && (c.c0 || c.c1)) {
-        const ImgDesc &D = A.img[g.im];
-        const size_t i0 = (size_t)gy * D.ld + c.gx0;
-        const float *u = D.u_hi[A.parity] + i0, *d = D.d + i0, *dl = D.delta + i0;
+        const size_t i0 = (size_t)gy * o.ld + c.gx0;
+        const float *u = o.u + i0, *d = o.d + i0, *dl = o.dl + i0;
         if (c.c0) {
             cp_async4(&O[0][0][p], u);
             cp_async4(&O[2][0][p], d);
@@ -420,13 +443,14 @@ __device__ __forceinline__ void out_fetch(const PairArgs &A, const Geo &g, const
     }
 }
 
-template <int MODE>
-__device__ __forceinline__ void out_finish(const PairArgs &A, const Geo &g, const OutCols &c, const float (*O)[2][128],
+// L2: the quadratic prox of the Anscombe L2 model, else the I-divergence prox (direct and Anscombe I-divergence
+// models), fixed per tile so that the step carries no model branch.
+template <int MODE, bool L2>
+__device__ __forceinline__ void out_finish(const OutImg &o, const Geo &g, const OutCols &c, const float (*O)[2][128],
                                            const uint4 (*Gb)[32], bool ring, int t, int p)
 {
     int Y, gy;
     if (!out_row(g, c, t, Y, gy) || !(c.c0 || c.c1)) return;
-    const ImgDesc &D = A.img[g.im];
     const uint4 e = Gb[Y][c.j];
     const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
     float gs0 = 0.0f, gs1 = 0.0f;
@@ -447,18 +471,18 @@ __device__ __forceinline__ void out_finish(const PairArgs &A, const Geo &g, cons
         if (c.mx0 >= 0) gs0 += g_at(Gb, Y, c.mx0) + (Ym >= 0 ? g_at(Gb, Ym, c.mx0) : 0.0f);
         if (c.mx1 >= 0) gs1 += g_at(Gb, Y, c.mx1) + (Ym >= 0 ? g_at(Gb, Ym, c.mx1) : 0.0f);
     }
-    const size_t i0 = (size_t)gy * D.ld + c.gx0;
+    const size_t i0 = (size_t)gy * o.ld + c.gx0;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (!(s ? c.c1 : c.c0)) continue;
         const float gv = s ? gs1 : gs0, uh = O[0][s][p], dd = O[2][s][p];
         if (MODE == kGrad) {
-            D.out[i0 + s] = gv + data_grad(uh, dd, D.model, D.sc.lambda);
+            o.out[i0 + s] = gv + data_grad(uh, dd, o.model, o.sc.lambda);
         } else {
             float nh, nd;
-            ipiano_update_f32(gv, uh, O[1][s][p], dd, D.model, D.sc, nh, nd);
-            D.u_hi[A.parity ^ 1][i0 + s] = nh;
-            D.delta[i0 + s] = nd;
+            ipiano_update_f32(gv, uh, O[1][s][p], dd, L2 ? kAnsL2 : kDirect, o.sc, nh, nd);
+            o.un[i0 + s] = nh;
+            o.dl[i0 + s] = nd;
         }
     }
 }
@@ -466,33 +490,44 @@ __device__ __forceinline__ void out_finish(const PairArgs &A, const Geo &g, cons
 // The output pass of the tile in partial-sum buffer k & 1 by the output warps, item p < 120 of every step: each
 // thread's operands are copied in kORing - 1 steps ahead, its row of a step is updated once the col2im of that M-tile
 // is done.  Returns false if the CTA gave up.
-template <int MODE>
-__device__ __forceinline__ bool output_tile(const PairArgs &A, PairSmem &S, int tile, int k, int p,
-                                            volatile int *abort_flag, int *status)
+template <int MODE, bool L2>
+__device__ __forceinline__ bool output_steps(const OutImg &o, PairSmem &S, const Geo &g, const OutCols &oc, bool ring,
+                                             int k, int p, volatile int *abort_flag, int *status)
 {
     const int b = k & 1;
-    const Geo g = pair_geometry(S, A.nimg, tile);
-    const bool ring = A.bc == kSymmetric && (g.ys < 3 || g.xs < 3 || g.ye > g.H - 3 || g.xe > g.W - 3);
-    OutCols oc = out_cols(g, p < 120 ? p : 0);
-    if (p >= 120) oc.c0 = oc.c1 = false;
     // one copy group per step (empty when the thread has no item), so that the group counts stay in step
     for (int t = 0; t < kORing - 1; ++t) {
-        out_fetch<MODE>(A, g, oc, S.O[t % kORing], t, p);
+        out_fetch<MODE>(o, g, oc, S.O[t % kORing], t, p);
         cp_async_commit();
     }
     bool ok = true;
     for (int t = 0; t < PNMT; ++t) {
-        out_fetch<MODE>(A, g, oc, S.O[(t + kORing - 1) % kORing], t + kORing - 1, p);
+        out_fetch<MODE>(o, g, oc, S.O[(t + kORing - 1) % kORing], t + kORing - 1, p);
         cp_async_commit();
         if (!mbar_wait_warp(&S.bar[B_CDONE + PNMT * b + t], (k >> 1) & 1, abort_flag, status)) {
             ok = false;
             break;
         }
         cp_async_wait<kORing - 1>();
-        out_finish<MODE>(A, g, oc, S.O[t % kORing], S.G[b], ring, t, p);
+        out_finish<MODE, L2>(o, g, oc, S.O[t % kORing], S.G[b], ring, t, p);
     }
     cp_async_wait<0>();
-    if (ok) mbar_arrive(&S.bar[B_GFREE + b]);
+    return ok;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool output_tile(const PairArgs &A, PairSmem &S, int tile, int k, int p,
+                                            volatile int *abort_flag, int *status)
+{
+    const Geo g = pair_geometry(S, A.nimg, tile);
+    const bool ring = A.bc == kSymmetric && (g.ys < 3 || g.xs < 3 || g.ye > g.H - 3 || g.xe > g.W - 3);
+    OutCols oc = out_cols(g, p < 120 ? p : 0);
+    if (p >= 120) oc.c0 = oc.c1 = false;
+    const OutImg o = out_img(A, g.im);
+    const bool ok = (MODE == kStep && o.model == kAnsL2)
+                        ? output_steps<MODE, true>(o, S, g, oc, ring, k, p, abort_flag, status)
+                        : output_steps<MODE, false>(o, S, g, oc, ring, k, p, abort_flag, status);
+    if (ok) mbar_arrive(&S.bar[B_GFREE + (k & 1)]);
     return ok;
 }
 
