@@ -89,7 +89,6 @@ constexpr uint32_t kOpsBytes = 16u * (WF_ENT + WA_ENT);
 constexpr uint32_t kUBoxBytes = 4u * PUC * PER;
 constexpr int kEItems = PER * 8;     // E build items (4 entries of one row each)
 constexpr int kBarProd = 1;          // named barrier of the staging warps
-constexpr int kORing = 4;            // output-pass operands are copied in kORing - 1 steps ahead
 
 // mbarriers
 constexpr int B_FWD = 0;      // [3] forward MMAs of M-tile g complete: R(g) ready           count 1 (commit)
@@ -115,7 +114,6 @@ struct PairSmem {
     uint4 Wa[WA_ENT];
     uint4 G[2][PRY][32];                 // vertical col2im partials: [buffer][output row][pair], the f16x2 words of
                                          // the four lane quarters in one 16-byte entry
-    float O[kORing][3][2][128];          // output-pass operands (u, delta, d of both pixels) of the next steps
     int tprefix[kMaxBatch + 1];
     int timg[kMaxBatch][3];              // tiles per row, H, W
     int live[kMaxBatch];                 // 0 once the image's stopping rule has held (its tiles are skipped)
@@ -362,9 +360,8 @@ __device__ __forceinline__ void build_e_item(const PairSmem &S, uint4 *E, int r,
 
 // Output pass of a tile, producer thread p < 120: the pair of columns j = 1 + p % 30 of output row 4t - 3 + p / 30
 // at step t.  The per-thread column geometry is fixed for the tile (OutCols); the operands (u, delta, d at both
-// pixels) are copied asynchronously into ring slot t % kORing some steps ahead (out_fetch, one cp.async group per
-// step, empty for items outside the write range); the update follows once the partial rows of the step are complete
-// (out_finish).
+// pixels) are loaded into registers two steps ahead (out_load); the update follows once the partial rows of the step
+// are complete (out_finish).
 struct OutCols {
     int j, r4, gx0;
     bool c0, c1;                         // columns 2j, 2j + 1 inside the tile's write range
@@ -422,32 +419,35 @@ __device__ __forceinline__ OutImg out_img(const PairArgs &A, int im)
     return o;
 }
 
+// u, delta, d of the pair's two pixels at one step
+struct OutVals {
+    float u[2], dl[2], d[2];
+};
+
+// Loads through L2 (ld.global.cg): delta is rewritten in this launch, by the same thread and after this load.
 template <int MODE>
-__device__ __forceinline__ void out_fetch(const OutImg &o, const Geo &g, const OutCols &c, float (*O)[2][128], int t,
-                                          int p)
+__device__ __forceinline__ OutVals out_load(const OutImg &o, const Geo &g, const OutCols &c, int t)
 {
+    OutVals v = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     int Y, gy;
-    if (t < PNMT && out_row(g, c, t, Y, gy) && (c.c0 || c.c1)) {
+    if (t < PNMT && out_row(g, c, t, Y, gy)) {
         const size_t i0 = (size_t)gy * o.ld + c.gx0;
-        const float *u = o.u + i0, *d = o.d + i0, *dl = o.dl + i0;
-        if (c.c0) {
-            cp_async4(&O[0][0][p], u);
-            cp_async4(&O[2][0][p], d);
-            if (MODE == kStep) cp_async4(&O[1][0][p], dl);
-        }
-        if (c.c1) {
-            cp_async4(&O[0][1][p], u + 1);
-            cp_async4(&O[2][1][p], d + 1);
-            if (MODE == kStep) cp_async4(&O[1][1][p], dl + 1);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (!(s ? c.c1 : c.c0)) continue;
+            v.u[s] = __ldcg(o.u + i0 + s);
+            v.d[s] = __ldcg(o.d + i0 + s);
+            if (MODE == kStep) v.dl[s] = __ldcg(o.dl + i0 + s);
         }
     }
+    return v;
 }
 
 // L2: the quadratic prox of the Anscombe L2 model, else the I-divergence prox (direct and Anscombe I-divergence
 // models), fixed per tile so that the step carries no model branch.
 template <int MODE, bool L2>
-__device__ __forceinline__ void out_finish(const OutImg &o, const Geo &g, const OutCols &c, const float (*O)[2][128],
-                                           const uint4 (*Gb)[32], bool ring, int t, int p)
+__device__ __forceinline__ void out_finish(const OutImg &o, const Geo &g, const OutCols &c, const OutVals &v,
+                                           const uint4 (*Gb)[32], bool ring, int t)
 {
     int Y, gy;
     if (!out_row(g, c, t, Y, gy) || !(c.c0 || c.c1)) return;
@@ -475,12 +475,12 @@ __device__ __forceinline__ void out_finish(const OutImg &o, const Geo &g, const 
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (!(s ? c.c1 : c.c0)) continue;
-        const float gv = s ? gs1 : gs0, uh = O[0][s][p], dd = O[2][s][p];
+        const float gv = s ? gs1 : gs0, uh = v.u[s], dd = v.d[s];
         if (MODE == kGrad) {
             o.out[i0 + s] = gv + data_grad(uh, dd, o.model, o.sc.lambda);
         } else {
             float nh, nd;
-            ipiano_update_f32(gv, uh, O[1][s][p], dd, L2 ? kAnsL2 : kDirect, o.sc, nh, nd);
+            ipiano_update_f32(gv, uh, v.dl[s], dd, L2 ? kAnsL2 : kDirect, o.sc, nh, nd);
             o.un[i0 + s] = nh;
             o.dl[i0 + s] = nd;
         }
@@ -488,31 +488,22 @@ __device__ __forceinline__ void out_finish(const OutImg &o, const Geo &g, const 
 }
 
 // The output pass of the tile in partial-sum buffer k & 1 by the output warps, item p < 120 of every step: each
-// thread's operands are copied in kORing - 1 steps ahead, its row of a step is updated once the col2im of that M-tile
-// is done.  Returns false if the CTA gave up.
+// thread's operands are loaded two steps ahead, its row of a step is updated once the col2im of that M-tile is done.
+// Returns false if the CTA gave up.
 template <int MODE, bool L2>
 __device__ __forceinline__ bool output_steps(const OutImg &o, PairSmem &S, const Geo &g, const OutCols &oc, bool ring,
-                                             int k, int p, volatile int *abort_flag, int *status)
+                                             int k, volatile int *abort_flag, int *status)
 {
     const int b = k & 1;
-    // one copy group per step (empty when the thread has no item), so that the group counts stay in step
-    for (int t = 0; t < kORing - 1; ++t) {
-        out_fetch<MODE>(o, g, oc, S.O[t % kORing], t, p);
-        cp_async_commit();
-    }
-    bool ok = true;
+    OutVals v0 = out_load<MODE>(o, g, oc, 0), v1 = out_load<MODE>(o, g, oc, 1);
     for (int t = 0; t < PNMT; ++t) {
-        out_fetch<MODE>(o, g, oc, S.O[(t + kORing - 1) % kORing], t + kORing - 1, p);
-        cp_async_commit();
-        if (!mbar_wait_warp(&S.bar[B_CDONE + PNMT * b + t], (k >> 1) & 1, abort_flag, status)) {
-            ok = false;
-            break;
-        }
-        cp_async_wait<kORing - 1>();
-        out_finish<MODE, L2>(o, g, oc, S.O[t % kORing], S.G[b], ring, t, p);
+        const OutVals v2 = out_load<MODE>(o, g, oc, t + 2);
+        if (!mbar_wait_warp(&S.bar[B_CDONE + PNMT * b + t], (k >> 1) & 1, abort_flag, status)) return false;
+        out_finish<MODE, L2>(o, g, oc, v0, S.G[b], ring, t);
+        v0 = v1;
+        v1 = v2;
     }
-    cp_async_wait<0>();
-    return ok;
+    return true;
 }
 
 template <int MODE>
@@ -525,8 +516,8 @@ __device__ __forceinline__ bool output_tile(const PairArgs &A, PairSmem &S, int 
     if (p >= 120) oc.c0 = oc.c1 = false;
     const OutImg o = out_img(A, g.im);
     const bool ok = (MODE == kStep && o.model == kAnsL2)
-                        ? output_steps<MODE, true>(o, S, g, oc, ring, k, p, abort_flag, status)
-                        : output_steps<MODE, false>(o, S, g, oc, ring, k, p, abort_flag, status);
+                        ? output_steps<MODE, true>(o, S, g, oc, ring, k, abort_flag, status)
+                        : output_steps<MODE, false>(o, S, g, oc, ring, k, abort_flag, status);
     if (ok) mbar_arrive(&S.bar[B_GFREE + (k & 1)]);
     return ok;
 }
