@@ -803,7 +803,6 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         int k = 0;
         for (int tile = tile0; ok && tile < ntiles; tile = next(tile + stride), ++k)
             ok = output_tile<MODE>(A, S, tile, k, tid - 32 * OUTW0, abort_flag, status);
-        cp_async_wait<0>();
     } else {
         // ---------------- staging: input regions and E operands, one tile ahead ----------------
         const int p = tid - 32 * STGW0;
