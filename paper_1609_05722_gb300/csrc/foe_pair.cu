@@ -32,7 +32,7 @@
 // tile's input region (one TMA box; for border tiles under symmetric padding the reflected ring is then filled in
 // from the box) and build its E operand (double-buffered) while the current tile runs; the output warps run the
 // output pass (padding fold, iPiano step) of the current tile row by row as the col2im warps finish its M-tiles,
-// with their operands copied in asynchronously a few M-tiles ahead.  No role waits for a whole-CTA barrier between
+// with their operands loaded into registers two M-tiles ahead.  No role waits for a whole-CTA barrier between
 // tiles.  Tensor memory holds three stages of R (96 columns), two of Psi (48) and two of Z2 (64); M-tile g (counted
 // over all tiles of the CTA) uses R stage g % 3 and Psi / Z2 stage g % 2.  An R stage is free for the forward MMAs
 // of M-tile g + 3 as soon as the expert warps have loaded R(g), so the forward MMAs run ahead of the adjoint.  Every mbarrier wait is bounded: on expiry the CTA records FOE_ETIMEOUT in *status, the
