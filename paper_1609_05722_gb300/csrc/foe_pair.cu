@@ -849,7 +849,10 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         cp_async_wait<0>();
     }
 
-    // every MMA issued by the two MMA warps is complete before tensor memory is released
+    // every MMA issued by the two MMA warps is complete before tensor memory is released.  If this bounded wait
+    // expired the launch has already recorded FOE_ETIMEOUT and its results are discarded; the columns are released
+    // all the same: a CTA must free its tensor memory before it exits, and columns left allocated would hold every
+    // later CTA of the SM in tcgen05.alloc
     if (warp == FWDW || warp == ADJW) {
         uint64_t *bar = &S.bar[B_DRAIN + (warp == FWDW ? 0 : 1)];
         commit_elect(bar);

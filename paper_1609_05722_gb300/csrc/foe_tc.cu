@@ -732,7 +732,10 @@ __global__ void __launch_bounds__(NTHR, (MODE == kHvp || MODE == kHess) ? 1 : 2)
         cp_async_commit();
     }
 
-    // every MMA issued by the two MMA threads is complete before tensor memory is released
+    // every MMA issued by the two MMA threads is complete before tensor memory is released.  If this bounded wait
+    // expired the launch has already recorded FOE_ETIMEOUT and its results are discarded; the columns are released
+    // all the same: a CTA must free its tensor memory before it exits, and columns left allocated would hold every
+    // later CTA of the SM in tcgen05.alloc
     if (warp == FWD_WARP || warp == ADJ_WARP) {
         uint64_t *bar = &S.bar[B_DRAIN + (warp == FWD_WARP ? 0 : 1)];
         commit_elect(bar);
