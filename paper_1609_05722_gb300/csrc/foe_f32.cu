@@ -22,6 +22,8 @@ constexpr int CH = 8;                       // filters per chunk
 constexpr int NTHREADS = 256;
 constexpr int RESP_ROWS = T + 6;            // responses on tile-relative rows [-3, 35)
 constexpr int RESP_STRIPS_X = (T + 8) / 2;  // 1x2 strips over cols [-4, 36)
+constexpr int NSTRIPS = RESP_ROWS * RESP_STRIPS_X;
+constexpr int NSTRIP = (NSTRIPS + NTHREADS - 1) / NTHREADS;  // strips per thread: 3
 
 struct F32Smem {
     float u[PLANE];
@@ -95,34 +97,52 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
 
     for (int ch = 0; ch < A.nchunks; ++ch) {
         // ---- forward responses and expert derivative on the response region ----
-        for (int s = tid; s < RESP_ROWS * RESP_STRIPS_X; s += NTHREADS) {
-            const int ry = s / RESP_STRIPS_X - kR, rx0 = (s % RESP_STRIPS_X) * 2 - 4;
-            float acc0[CH], acc1[CH];
+        // each thread computes its NSTRIP strips s = tid + k NTHREADS together, so that every weight load serves all
+        // of them (a thread without a k-th strip computes a copy of its first one and discards it)
+        float acc[NSTRIP][2][CH];
 #pragma unroll
-            for (int f = 0; f < CH; ++f) acc0[f] = acc1[f] = 0.0f;
+        for (int k = 0; k < NSTRIP; ++k)
+#pragma unroll
+            for (int f = 0; f < CH; ++f) acc[k][0][f] = acc[k][1][f] = 0.0f;
+        int sk[NSTRIP];
+#pragma unroll
+        for (int k = 0; k < NSTRIP; ++k) {
+            const int sv = tid + k * NTHREADS;
+            sk[k] = sv < NSTRIPS ? sv : tid;
+        }
 #pragma unroll 1
-            for (int a = 0; a < kKS; ++a) {
+        for (int a = 0; a < kKS; ++a) {
+            float v[NSTRIP][8];
+#pragma unroll
+            for (int k = 0; k < NSTRIP; ++k) {
+                const int ry = sk[k] / RESP_STRIPS_X - kR, rx0 = (sk[k] % RESP_STRIPS_X) * 2 - 4;
                 const float *urow = &S.u[(ry + a - kR + R0) * UCOLS + (rx0 - kR + C0)];
-                float v[8];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float2 q = *reinterpret_cast<const float2 *>(urow + 2 * j);
-                    v[2 * j] = q.x;
-                    v[2 * j + 1] = q.y;
-                }
-#pragma unroll
-                for (int b = 0; b < kKS; ++b) {
-                    const float *wp = &S.wf[(ch * kKK + a * kKS + b) * CH];
-                    const float4 w0 = *reinterpret_cast<const float4 *>(wp);
-                    const float4 w1 = *reinterpret_cast<const float4 *>(wp + 4);
-                    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                    for (int f = 0; f < CH; ++f) {
-                        acc0[f] = fmaf(wv[f], v[b], acc0[f]);
-                        acc1[f] = fmaf(wv[f], v[b + 1], acc1[f]);
-                    }
+                    v[k][2 * j] = q.x;
+                    v[k][2 * j + 1] = q.y;
                 }
             }
+#pragma unroll
+            for (int b = 0; b < kKS; ++b) {
+                const float *wp = &S.wf[(ch * kKK + a * kKS + b) * CH];
+                const float4 w0 = *reinterpret_cast<const float4 *>(wp);
+                const float4 w1 = *reinterpret_cast<const float4 *>(wp + 4);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int k = 0; k < NSTRIP; ++k)
+#pragma unroll
+                    for (int f = 0; f < CH; ++f) {
+                        acc[k][0][f] = fmaf(wv[f], v[k][b], acc[k][0][f]);
+                        acc[k][1][f] = fmaf(wv[f], v[k][b + 1], acc[k][1][f]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NSTRIP; ++k) {
+            if (tid + k * NTHREADS >= NSTRIPS) continue;
+            const int ry = sk[k] / RESP_STRIPS_X - kR, rx0 = (sk[k] % RESP_STRIPS_X) * 2 - 4;
             const int gy = ty0 + ry;
 #pragma unroll
             for (int px = 0; px < 2; ++px) {
@@ -133,7 +153,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
                         float es = 0.0f;
 #pragma unroll
                         for (int f = 0; f < CH; ++f) {
-                            const float r = px ? acc1[f] : acc0[f];
+                            const float r = acc[k][px][f];
                             es = fmaf(S.wa[((ch * CH + f) * kKS + kKS - 1) * 8 + 7], log1pf(r * r), es);
                         }
                         eacc += (double)es;
@@ -141,7 +161,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_foe_f32(const __grid_constant__
                 } else {
 #pragma unroll
                     for (int f = 0; f < CH; ++f) {
-                        const float r = px ? acc1[f] : acc0[f];
+                        const float r = acc[k][px][f];
                         S.psi[f * PLANE + (ry + R0) * UCOLS + (rx + C0)] = in ? __fdividef(r, fmaf(r, r, 1.0f)) : 0.0f;
                     }
                 }
