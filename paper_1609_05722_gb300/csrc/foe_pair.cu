@@ -814,8 +814,10 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
         auto land = [&](const Geo &gr) {
             // wait for the staged region, then fill its reflected ring (symmetric padding, TMA-staged)
             bool w = mbar_wait(&S.bar[B_ULAND], ucount & 1, abort_flag, status);
-            ++ucount;
-            pending = false;
+            if (w) {
+                ++ucount;
+                pending = false;         // otherwise the copy may still be in flight: drained before the CTA leaves
+            }
             if (!prod_all(w)) return false;
             if (A.bc == kSymmetric && gr.W >= PUC && gr.H >= PER && region_outside(gr)) {
                 fill_ring(S, gr, r_next, p);
