@@ -3,6 +3,8 @@ that include/foe.h declares, and its host-only logic (argument checks, step size
 import ctypes as C
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -88,3 +90,39 @@ def test_mma_cost_rejects_bad_shapes_on_the_host(lib, args):
     out = C.c_double(-1.0)
     assert lib.foe_mma_cost(*args, C.byref(out)) == F.FOE_EINVAL
     assert out.value == -1.0
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "foe.h"
+
+int main(void)
+{
+    foe_solve_opts o;
+    double out = -1.0;
+    if (foe_default_opts(&o) != FOE_OK) return 1;
+    if (o.iters != 300 || o.model != FOE_MODEL_AUTO || o.prec != FOE_PREC_BF16) return 2;
+    if (strcmp(foe_status_string(FOE_EINVAL), "invalid argument") != 0) return 3;
+    if (foe_mma_cost(100, 64, 0, 0, 2, 16, &out) != FOE_EINVAL || out != -1.0) return 4;
+    puts("ok");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    # the boundary is a C ABI: a C99 program includes the header with every warning an error, links against the
+    # library and calls its host-only entry points (no GPU needed)
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src, exe = tmp_path / "client.c", tmp_path / "client"
+    src.write_text(C_CLIENT)
+    libdir = os.path.dirname(B.LIB)
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", f"-I{os.path.dirname(HEADER)}", str(src),
+           f"-L{libdir}", "-lfoe", f"-Wl,-rpath,{libdir}", "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
