@@ -637,8 +637,10 @@ __global__ void __launch_bounds__(NT, 1) k_foe_pair(const __grid_constant__ Pair
                     const bool row_in = gy >= 0 && gy < g.H;
                     const uint32_t k0 = (row_in && gx0 >= 0 && gx0 < g.W) ? 0xFFFFFFFFu : 0u;
                     const uint32_t k1 = (row_in && gx0 + 1 >= 0 && gx0 + 1 < g.W) ? 0xFFFFFFFFu : 0u;
+                    // (most M-tiles of a border tile lie inside the image: then there is nothing to clear)
+                    if (!__all_sync(0xffffffffu, (k0 & k1) != 0u))
 #pragma unroll
-                    for (int m = 0; m < kExpCols / 2; ++m) w[m] &= (kExpCols * c + 2 * m < 48) ? k0 : k1;
+                        for (int m = 0; m < kExpCols / 2; ++m) w[m] &= (kExpCols * c + 2 * m < 48) ? k0 : k1;
                 }
                 // the Psi stage is free once the adjoint MMAs of M-tile g - NPST (its previous reader) are complete
                 if (gm >= NPST && !mbar_wait_warp(&S.bar[B_PFREE + ps], pph ^ 1u, abort_flag, status)) {
